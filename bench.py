@@ -1,0 +1,331 @@
+"""Benchmark: Wang-Landau spin-flip trials/s of two-dimensional REWL on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+One step is one cycle of the whole sampling path on the synthetic workload:
+every walker does `exchange_interval` single-spin-flip trials (Eq. 1 and the
+update of Sec. 2), one replica-exchange sweep (Eq. 2) and the flatness check /
+iteration advance (Sec. 2-3).  The default workload is 2D REWL of the 8 x 8
+periodic Ising model: 3 x 3 (E, M) windows at 75% overlap, 4 walkers per
+window, exchange every 10^4 trials per walker.
+
+value    trials/s with the run resident in HBM, CUDA events on the run's stream
+         around each step, L2 flushed (256 MiB write) between steps;
+e2e      the same metric through the C ABI with host buffers: creation from
+         host spin bytes (host->device), K synchronous steps each reading the
+         run status back (device->host), and the joined ln g(E,M) copied to
+         host memory, wall clock;
+roofline the sampling kernel (the dominant one) against the ALU peak:
+         algorithmic integer/float operations per trial x trials per launch /
+         mean launch time from its own CUDA events in the timed steps;
+cpu_baseline the CPU oracle (test infrastructure, single thread) on a bounded
+         sample of the same workload.
+With --impl reference the CPU oracle is the timed implementation.
+Under torchrun with N > 1 ranks each rank runs an independent replica of the
+run on its own GPU (the method's windows share one GPU; replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1508_02748_gb300 import workloads  # noqa: E402
+
+METRIC = "WL spin-flip trials/s & time-to-ln f=1e-6 at fixed ln g error, batched vs plain"
+# Algorithmic operations per trial (integer and float ALU), counted from the
+# method: half a Philox4x32-10 call (10 rounds x 10 ops / 2 trials = 50), the
+# float log of u (~15), site/row/column and 5 spin-bit extractions with the
+# periodic neighbours (~25), bin move, window test and table index (~12),
+# the screened acceptance (~10) and the bookkeeping of ln g / H (~8).
+OPS_PER_TRIAL = 120
+ALU_LANES_PER_SM = 128          # 32-bit lanes per SM (4 partitions x 32)
+FALLBACK_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default=workloads.REWL_L8.name, choices=sorted(workloads.ALL))
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle --
+
+def oracle_rate(w, seconds: float) -> dict:
+    """Trials/s of the CPU oracle on a bounded sample: the workload's run,
+    whole cycles until `seconds` of CPU time have passed."""
+    import oracle
+    ocfg = oracle.OracleConfig(L=w.L, n_win_E=w.n_win_E, n_win_M=w.n_win_M, overlap_E=w.overlap_E,
+                               overlap_M=w.overlap_M, walkers_per_window=w.walkers_per_window,
+                               lnf_init=w.lnf_init, lnf_final=w.lnf_final, lnf_factor=w.lnf_factor,
+                               flatness=w.flatness, exchange_interval=w.exchange_interval,
+                               check_every=w.check_every, seed=w.seed(0), drive_budget=10**8)
+    r = oracle.OracleREWL(ocfg)
+    nwalk = r.info()["nwalk"]
+    cyc = 0
+    t0 = time.perf_counter()
+    while True:
+        r.run_cycles(1)
+        cyc += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    trials = cyc * w.exchange_interval * nwalk
+    r.close()
+    return {"value": trials / dt, "unit": "trials/s", "cores": 1, "kind": "oracle",
+            "sample": f"{cyc} cycles of {w.name} ({trials} trials) in {dt:.1f} s, single thread"}
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    ocfg = oracle.OracleConfig(L=w.L, n_win_E=w.n_win_E, n_win_M=w.n_win_M, overlap_E=w.overlap_E,
+                               overlap_M=w.overlap_M, walkers_per_window=w.walkers_per_window,
+                               lnf_init=w.lnf_init, lnf_final=w.lnf_final, lnf_factor=w.lnf_factor,
+                               flatness=w.flatness, exchange_interval=w.exchange_interval,
+                               check_every=w.check_every, seed=w.seed(0), drive_budget=10**8)
+    r = oracle.OracleREWL(ocfg)
+    nwalk = r.info()["nwalk"]
+    # each step is a bounded sample: one cycle of the workload (one step of the path)
+    for _ in range(args.warmup):
+        r.run_cycles(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.run_cycles(1)
+    dt = time.perf_counter() - t0
+    trials = args.steps * w.exchange_interval * nwalk
+    value = trials / dt
+    line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": _config_dict(w, "none (CPU)"),
+            "cpu_baseline": {"value": value, "unit": "trials/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} cycles of {w.name}, single thread"},
+            "e2e": {"value": value, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config_dict(w, l2: str) -> dict:
+    return {"workload": w.name, "L": w.L, "windows": f"{w.n_win_E}x{w.n_win_M}",
+            "overlap": w.overlap_E, "walkers_per_window": w.walkers_per_window,
+            "walkers": w.n_walkers, "exchange_interval": w.exchange_interval,
+            "check_every": w.check_every, "ln_g": "fp64", "step": "one cycle: sample + exchange + check",
+            "l2": l2}
+
+
+# ------------------------------------------------------------------- GPU ----
+
+def run_gpu(args, w):
+    import numpy as np
+    import torch
+
+    import paper_1508_02748_gb300 as P
+    from paper_1508_02748_gb300 import build as pkg_build
+
+    rank, world, local = dist_env()
+    pkg_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    cfg = P.Config.from_workload(w, replicate=rank, drive_budget=10**8)
+    run = P.REWL(cfg, device=str(dev))
+    s = run.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    nwalk_active = run.status()["n_walkers"]
+    trials_per_step = w.exchange_interval * nwalk_active
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            run.enqueue_cycle()
+    s.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    with torch.cuda.stream(s):
+        for k in range(K):
+            flush.zero_()                                # L2 flush, outside the step's events
+            ev[k][0].record(s)
+            run.enqueue_cycle(P.PART_SAMPLE)
+            ev[k][1].record(s)
+            run.enqueue_cycle(P.PART_REST)
+            ev[k][2].record(s)
+            check = ((args.warmup + k + 1) % w.check_every) == 0
+            launches += 3 + (2 if check else 0)
+    s.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
+    sweep_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = run.status()
+    value = trials_per_step * K * world / (total_ms / 1e3)
+
+    # roofline of the sampling kernel: ALU operations of the method per launch
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 1920.0
+    peak_ops = sm_count * ALU_LANES_PER_SM * mhz * 1e6
+    sweep_s = statistics.mean(sweep_ms) / 1e3
+    achieved = OPS_PER_TRIAL * trials_per_step / sweep_s
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak_ops, "traffic": None,
+            "kernel": "k_sweep_fp64", "kernel_ms_mean": sweep_s * 1e3,
+            "kernel_share_of_step": sum(sweep_ms) / total_ms,
+            "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x median SM clock {mhz:.0f} MHz (derived)"}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        rng = np.random.default_rng(w.seed(rank) + 7)
+        host_spins = rng.integers(0, 2, size=(w.n_walkers, w.N), dtype=np.uint8)
+        pinned = torch.from_numpy(host_spins).pin_memory().numpy()
+        out = np.empty((w.N + 1) * (w.N + 1), dtype=np.float64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run2 = P.REWL(cfg, init_spins=pinned, device=str(dev), stream=s)
+        for _ in range(K):
+            run2.run_cycles(1)
+        J = run2.lng()
+        t1 = time.perf_counter()
+        out[:] = J.ravel()
+        e2e_trials = trials_per_step * K
+        status_bytes = 64
+        e2e = {"value": e2e_trials * world / (t1 - t0), "unit": "trials/s",
+               "h2d_bytes_per_step": (host_spins.nbytes + 128) / K,
+               "d2h_bytes_per_step": status_bytes + out.nbytes / K,
+               "includes": "create from host spins + drive, K synchronous steps with status readback, "
+                           "join + normalise + joined table to host"}
+        run2.close()
+
+    if rank == 0:
+        cpu = oracle_rate(w, args.cpu_seconds)
+        line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": _config_dict(w, "flushed between steps (256 MiB write, outside the step events)"),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
+                "clocks": clk,
+                "run": {"iteration": st["iteration"], "lnf": st["lnf"], "exch_accepts": st["exch_accepts"],
+                        "exch_attempts": st["exch_attempts"]}}
+        print(json.dumps(line), flush=True)
+    run.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = workloads.ALL[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * rewl.h -- C ABI of librewl: two-dimensional replica-exchange Wang-Landau
+ * (REWL) sampling of the joint density of states g(E,M) of the periodic L x L
+ * Ising model on one GPU (sm_103a).
+ *
+ * The method is that of Valentim et al., "Exploring Replica-Exchange
+ * Wang-Landau sampling in higher-dimensional parameter space"
+ * (arXiv:1508.02748): Wang-Landau walkers doing single-spin-flip trials with
+ * the acceptance of Eq. 1 and the g/H update of Sec. 2, in overlapping
+ * windows of (E, M) (Sec. 2, Fig. 1b), exchanging configurations between
+ * neighbouring windows with the acceptance of Eq. 2, all advancing to the
+ * next modification factor together once every histogram is flat (80%
+ * criterion, Sec. 3), and finally joined into one g(E,M) by the
+ * marginal/derivative matching of Eqs. 3-4 (Sec. 2, one axis at a time).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns int: REWL_OK (0) or a negative REWL_E_* code; no
+ *     exception crosses the ABI.  rewl_last_error() gives a message.
+ *   - Bins: e = (E + 2N)/4 in [0, N], m = (M + N)/2 in [0, N], N = L*L.  A
+ *     window is the integer rectangle [e0, e1] x [m0, m1].  Window index
+ *     win = b * n_win_E + a for the a-th window along E and b-th along M.
+ *     Walker index w = win * walkers_per_window + k.
+ *   - Device memory: the caller passes one device buffer (the workspace) of
+ *     at least rewl_workspace_size() bytes to rewl_create and keeps it alive
+ *     until rewl_destroy; the library allocates no device memory of its own
+ *     and never frees the workspace.  The handle itself is host memory owned
+ *     by the library (freed by rewl_destroy).
+ *   - Host pointers (host_*) are plain host memory owned by the caller; the
+ *     calls that take them copy synchronously.
+ *   - All device work is queued on the stream given to rewl_create (NULL =
+ *     the legacy default stream); every call returns after that work is
+ *     complete.
+ *   - A handle is not thread-safe.
+ */
+#ifndef REWL_H
+#define REWL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REWL_OK 0
+#define REWL_E_INVALID (-1)     /* bad argument or configuration */
+#define REWL_E_CUDA (-2)        /* a CUDA call failed (message has the CUDA error) */
+#define REWL_E_TIMEOUT (-3)     /* a bounded device wait gave up */
+#define REWL_E_UNREACHABLE (-4) /* a walker could not be driven into its window */
+#define REWL_E_OVERFLOW (-5)    /* a histogram entry would pass INT32_MAX */
+#define REWL_E_BUDGET (-6)      /* rewl_run_iteration: cycle budget used, not flat yet */
+#define REWL_E_JOIN (-7)        /* pieces cannot be joined (no common bins) */
+#define REWL_E_CAPACITY (-8)    /* output or workspace buffer too small */
+
+/* ln g arithmetic of the sampling tables. */
+#define REWL_FP64 0             /* double per bin */
+#define REWL_F32X2 1            /* compensated pair of floats (hi, lo) per bin */
+
+/* Sampling kernels (same trajectory, different mapping onto the GPU). */
+#define REWL_SAMPLER_WARP 0     /* 8/16/32 lanes per walker, 3/4/5 trials resolved per step */
+#define REWL_SAMPLER_THREAD 1   /* one thread per walker, one trial per step */
+
+/* What rewl_get_lng returns. */
+#define REWL_LNG_JOINED 0       /* (N+1) x (N+1) doubles, [e][m], sum g = 2^N */
+#define REWL_LNG_MARGINAL_E 1   /* N+1 doubles: ln sum_m g(e, m) of the joined table (Eq. 3) */
+
+typedef struct rewl_s rewl_t;   /* opaque */
+
+/* Run configuration (the paper's statement of the problem, Sec. 2-3). */
+typedef struct rewl_config {
+    uint32_t struct_size;       /* sizeof(rewl_config) */
+    int32_t L;                  /* lattice side, 4 <= L <= 64; N = L*L spins */
+    int32_t n_win_E;            /* windows along E (Sec. 2, Fig. 1b) */
+    int32_t n_win_M;            /* windows along M (Sec. 2: "splitting both") */
+    double overlap_E;           /* overlap fraction of adjacent windows, [0, 1) */
+    double overlap_M;
+    int32_t walkers_per_window; /* independent walkers per window (Sec. 2), >= 1 */
+    int32_t precision;          /* REWL_FP64 or REWL_F32X2 */
+    double lnf_init;            /* ln f of the first iteration (> 0) */
+    double lnf_final;           /* run ends after the first flat iteration with ln f <= this */
+    double lnf_factor;          /* ln f <- ln f * factor; 0.5 is f -> sqrt(f) (Sec. 2) */
+    double flatness;            /* min H >= flatness * mean H (0.8, Sec. 3); six decimals */
+    uint64_t exchange_interval; /* trials per walker between exchange sweeps (Sec. 2) */
+    int32_t check_every;        /* cycles between flatness checks, >= 1 */
+    int32_t walkers_per_block;  /* sampling-kernel tiling (0 = automatic) */
+    int32_t sampler;            /* REWL_SAMPLER_WARP (default) or REWL_SAMPLER_THREAD */
+    int32_t lanes_per_walker;   /* warp sampler: 8, 16 or 32 lanes per walker (0 = automatic) */
+    uint64_t seed;              /* Philox key of every random draw */
+    uint64_t drive_budget;      /* steps allowed to drive a walker into its window */
+} rewl_config;
+
+/* Snapshot of a run. */
+typedef struct rewl_status {
+    int32_t iteration;          /* completed iterations (flat events) */
+    int32_t done;               /* 1 once the final iteration is flat */
+    double lnf;                 /* ln f of the current iteration */
+    uint64_t cycles;            /* sample/exchange cycles run */
+    uint64_t trials;            /* trials per walker run so far */
+    uint64_t exch_attempts;     /* exchange attempts (both walkers in the overlap) */
+    uint64_t exch_accepts;
+    int32_t n_flat;             /* walkers found flat at the last check */
+    int32_t n_walkers;          /* walkers of non-empty windows */
+    int32_t error;              /* device error word (0 = none) */
+    int32_t reserved;
+} rewl_status;
+
+/* Bytes of device workspace a configuration needs.  Returns REWL_E_INVALID
+ * for an invalid configuration. */
+int rewl_workspace_size(const rewl_config *cfg, size_t *bytes);
+
+/* Creates a run: window geometry (equal-sized overlapping windows; windows
+ * with no possible (E, M) bin are left empty and get no walkers), initial
+ * spins, and the drive of every walker into its window.
+ *   host_init_spins: NULL to draw i.i.d. +-1 spins from the seed, else
+ *     n_walkers * N bytes (0 = down, 1 = up), walker-major, site = i*L + j.
+ *   d_workspace: device buffer of >= rewl_workspace_size() bytes, 256-byte
+ *     aligned, owned by the caller.
+ *   stream: a cudaStream_t (NULL = default stream).
+ * Errors: REWL_E_INVALID, REWL_E_CAPACITY (workspace too small),
+ * REWL_E_UNREACHABLE (drive budget exhausted), REWL_E_CUDA. */
+int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_workspace,
+                size_t workspace_bytes, void *stream, rewl_t **out);
+
+/* Runs n_cycles cycles.  One cycle: every walker does exchange_interval
+ * trials (Eq. 1 and the Sec. 2 update), one exchange sweep (Eq. 2) of the
+ * phase cycle mod 4 (E-even, E-odd, M-even, M-odd pairs of adjacent
+ * windows), and every check_every cycles a flatness check over all walkers;
+ * when every walker is flat the iteration ends (H reset, ln f * factor) or,
+ * if ln f <= lnf_final, the run is done.  Cycles after done do nothing.
+ * status may be NULL. */
+int rewl_run_cycles(rewl_t *h, uint64_t n_cycles, rewl_status *status);
+
+/* Runs cycles until an iteration ends (or the run is done): REWL_OK; or
+ * until max_cycles cycles ran without that: REWL_E_BUDGET. */
+int rewl_run_iteration(rewl_t *h, uint64_t max_cycles, rewl_status *status);
+
+/* Parts of one cycle for rewl_enqueue_cycle. */
+#define REWL_PART_SAMPLE 1      /* the exchange_interval trials of every walker */
+#define REWL_PART_REST 2        /* exchange sweep, flatness check (every check_every cycles), counters */
+
+/* Queues one cycle, or the given parts of it in order SAMPLE then REST, on
+ * the run's stream and returns without waiting: the asynchronous form of
+ * rewl_run_cycles(h, 1, NULL) for callers that synchronise or time the
+ * stream themselves (a cycle is counted when its REST part is queued).
+ * Errors are those of queueing (REWL_E_INVALID, REWL_E_CUDA); device errors
+ * surface at the next synchronous call. */
+int rewl_enqueue_cycle(rewl_t *h, int parts);
+
+/* Single steps (also used inside the cycle): n trials per walker; one
+ * exchange sweep of the current phase; one flatness check with advance. */
+int rewl_sweep(rewl_t *h, uint64_t n_trials);
+int rewl_exchange(rewl_t *h);
+int rewl_check(rewl_t *h, int32_t *all_flat);
+
+int rewl_get_status(rewl_t *h, rewl_status *status);
+
+/* Window rectangles: n_windows x 5 int32 (e0, e1, m0, m1, non-empty). */
+int rewl_get_windows(rewl_t *h, int32_t *host_out, size_t capacity);
+
+/* Walker state: n_walkers x 4 int64 (e, m, trials, last flat verdict) and
+ * optionally spins n_walkers x N bytes (0/1, site = i*L + j). */
+int rewl_get_walkers(rewl_t *h, int64_t *host_state, uint8_t *host_spins);
+
+/* Per-walker tables, walker-major, each window_bins = (e1-e0+1)(m1-m0+1)
+ * entries in [e][m] order: ln g as double (converted from the compensated
+ * pair for REWL_F32X2) and H as int32 (-1 = never visited).  Either pointer
+ * may be NULL.  capacity counts entries per array. */
+int rewl_get_tables(rewl_t *h, double *host_lng, int32_t *host_H, size_t capacity);
+/* Overwrites the tables (tests set up join and flatness cases with it). */
+int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t *host_H, size_t count);
+
+/* Final merge of each window's walkers, join (Eqs. 3-4, E then M) and
+ * normalisation to sum g = 2^N, all on the device, copied to host_out.
+ * what = REWL_LNG_JOINED or REWL_LNG_MARGINAL_E.  *needed gets the entry
+ * count; REWL_E_CAPACITY if capacity is smaller.  host_ematch (n_win_M x
+ * (n_win_E - 1) int32) and host_mmatch (n_win_M - 1) receive the matching
+ * points (-1 where unused) and may be NULL.  REWL_E_JOIN when two adjacent
+ * pieces share no visited bin. */
+int rewl_get_lng(rewl_t *h, int what, double *host_out, size_t capacity, size_t *needed,
+                 int32_t *host_ematch, int32_t *host_mmatch);
+
+/* Message of the last failing call on h (never NULL). */
+const char *rewl_last_error(const rewl_t *h);
+
+/* Releases the handle (not the workspace). */
+int rewl_destroy(rewl_t *h);
+
+/* Device Philox4x32-10 (the generator every random draw of the library uses;
+ * Salmon et al., SC'11): d_out[4i..4i+3] = Philox(d_ctr[4i..4i+3], key).
+ * d_ctr, d_out: device pointers to 4n uint32; key: host pointer to 2 uint32. */
+int rewl_philox(const uint32_t *d_ctr, const uint32_t *key, uint32_t *d_out, uint64_t n,
+                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REWL_H */

@@ -1,0 +1,10 @@
+"""GB300-native two-dimensional replica-exchange Wang-Landau sampling.
+
+The sampling path (Wang-Landau trials, replica exchange, flatness checks,
+iteration advance, merge/join/normalisation) runs in the CUDA kernels of
+``librewl.so`` behind the C ABI of ``include/rewl.h``; :mod:`.rewl` is its
+argument-marshalling binding.  Nothing is loaded at import time; the first
+:class:`REWL` loads the library and fails loudly if it is missing.
+"""
+from .rewl import (F32X2, FP64, LNG_JOINED, LNG_MARGINAL_E, PART_REST, PART_SAMPLE, REWL,  # noqa: F401
+                   SAMPLER_THREAD, SAMPLER_WARP, Config, REWLError, load_library, philox)

@@ -1,0 +1,686 @@
+// C ABI of librewl (include/rewl.h): window geometry, workspace layout,
+// run orchestration (cycles of sample -> exchange -> check, replayed as CUDA
+// graphs), state access and the final join.  Every arithmetic step of the
+// method runs in the kernels of rewl_kernels.cu and rewl_join.cu; this file
+// only sets up integer geometry and queues work.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rewl_internal.cuh"
+
+using namespace rewl;
+
+struct rewl_s {
+    rewl_config cfg;
+    Params p;
+    JoinScratch j;
+    cudaStream_t stream;
+    char err[512];
+    unsigned long long host_cycle;   // cycles queued (equals the device count until done)
+    int max_pairs;
+    int wpb;
+    int32_t *d_fail;
+    uint8_t *d_stage;                // staging bytes (aliases the joined table)
+    cudaGraphExec_t graph;           // check_every cycles, the last one checking
+    bool graph_ok;
+    int first_active;                // a walker of a non-empty window (-1 if none)
+};
+
+namespace {
+
+const char *g_noerr = "";
+char g_create_err[512];
+
+int fail(rewl_t *h, int code, const char *fmt, ...)
+{
+    char *dst = h ? h->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), REWL_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ----------------------------------------------------------- geometry ----
+
+// Equal-sized overlapping windows over `bins` bins (Sec. 2, Fig. 1b; Sec. 3
+// "equal-sized windows"): width ceil(bins / (1 + (n-1)(1-overlap))), the n
+// starts spread evenly over [0, bins - width], rounded half up.
+void axis_windows(int bins, int n, double overlap, std::vector<int> &lo, std::vector<int> &hi)
+{
+    lo.assign(n, 0);
+    hi.assign(n, bins - 1);
+    if (n == 1) return;
+    const double denom = 1.0 + (double)(n - 1) * (1.0 - overlap);
+    const double ratio = (double)bins / denom;
+    long long width = (long long)std::ceil(ratio);
+    if (width > bins) width = bins;
+    if (width < 1) width = 1;
+    const long long slack = bins - width;
+    for (int k = 0; k < n; ++k) {
+        const long long twice = 2LL * k * slack + (n - 1);   // round half up of k*slack/(n-1)
+        lo[k] = (int)(twice / (2LL * (n - 1)));
+        hi[k] = lo[k] + (int)width - 1;
+    }
+}
+
+// A bin (e, m) can hold a configuration only if its broken-bond count
+// b = 2e lies between the fewest bonds a minority of k = min(m, N-m) spins
+// must break (compact droplet, 2 ceil(2 sqrt k), or a stripe wrapping the
+// torus, 2L plus 2 when k is not a multiple of L) and the most it can break
+// (4 per minority spin: b <= 2N - 2|2m - N|).  Sec. 1: the (E, M) plane has
+// empty regions; windows inside them get no walkers.
+bool bin_can_hold(int L, int e, int m)
+{
+    const int N = L * L;
+    const int k = std::min(m, N - m);
+    const int broken = 2 * e;
+    if (broken > 2 * N - 2 * std::abs(2 * m - N)) return false;
+    if (k == 0) return broken == 0;
+    int c = (int)std::floor(2.0 * std::sqrt((double)k));
+    while (c * c < 4 * k) ++c;                 // c = ceil(2 sqrt k), exactly
+    while (c > 0 && (c - 1) * (c - 1) >= 4 * k) --c;
+    const int droplet = 2 * c;
+    const int stripe = 2 * L + (k % L ? 2 : 0);
+    return broken >= std::min(droplet, stripe);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t st, rect, active, spins, we, wm, wt, wflat, lng, H;
+    size_t piece, off, GE, eshift, efrom, eto, ematch, rowok, F, mshift, mfrom, mto, mmatch, J, red, marg, gbuf;
+    size_t fail, total;
+};
+
+struct Dims {
+    int L, N, wpr, nwords, nE, nM, W, nwin, nwalk, wE, wM, T;
+    long long tstride;
+};
+
+int check_config(const rewl_config *c, const char **why)
+{
+    if (!c) { *why = "null config"; return REWL_E_INVALID; }
+    if (c->struct_size != sizeof(rewl_config)) { *why = "struct_size mismatch"; return REWL_E_INVALID; }
+    if (c->L < 4 || c->L > 64) { *why = "L must be in [4, 64]"; return REWL_E_INVALID; }
+    const int N = c->L * c->L;
+    if (c->n_win_E < 1 || c->n_win_M < 1 || c->n_win_E > N + 1 || c->n_win_M > N + 1) { *why = "bad window grid"; return REWL_E_INVALID; }
+    if (!(c->overlap_E >= 0.0 && c->overlap_E < 1.0 && c->overlap_M >= 0.0 && c->overlap_M < 1.0)) { *why = "overlap must be in [0, 1)"; return REWL_E_INVALID; }
+    if (c->walkers_per_window < 1 || c->walkers_per_window > 1024) { *why = "walkers_per_window must be in [1, 1024]"; return REWL_E_INVALID; }
+    if (c->precision != REWL_FP64 && c->precision != REWL_F32X2) { *why = "unknown precision"; return REWL_E_INVALID; }
+    if (c->precision != REWL_FP64) { *why = "REWL_F32X2 sampling is not built yet"; return REWL_E_INVALID; }
+    if (!(c->lnf_init > 0.0 && c->lnf_final > 0.0 && c->lnf_factor > 0.0 && c->lnf_factor < 1.0)) { *why = "bad ln f schedule"; return REWL_E_INVALID; }
+    if (!(c->flatness > 0.0 && c->flatness <= 1.0)) { *why = "flatness must be in (0, 1]"; return REWL_E_INVALID; }
+    if (c->exchange_interval < 1) { *why = "exchange_interval must be >= 1"; return REWL_E_INVALID; }
+    if (c->check_every < 1) { *why = "check_every must be >= 1"; return REWL_E_INVALID; }
+    if (c->walkers_per_block < 0 || c->walkers_per_block > 128) { *why = "walkers_per_block must be in [0, 128]"; return REWL_E_INVALID; }
+    if (c->sampler != REWL_SAMPLER_WARP && c->sampler != REWL_SAMPLER_THREAD) { *why = "unknown sampler"; return REWL_E_INVALID; }
+    if (c->sampler == REWL_SAMPLER_WARP && c->walkers_per_block > 8) { *why = "warp sampler: walkers_per_block (warps per block) must be in [0, 8]"; return REWL_E_INVALID; }
+    if (c->lanes_per_walker != 0 && c->lanes_per_walker != 8 && c->lanes_per_walker != 16 && c->lanes_per_walker != 32) { *why = "lanes_per_walker must be 0, 8, 16 or 32"; return REWL_E_INVALID; }
+    return REWL_OK;
+}
+
+Dims dims_of(const rewl_config *c)
+{
+    Dims d;
+    d.L = c->L; d.N = c->L * c->L;
+    d.wpr = (c->L + 31) / 32;
+    d.nwords = d.L * d.wpr;
+    d.nE = c->n_win_E; d.nM = c->n_win_M; d.W = c->walkers_per_window;
+    d.nwin = d.nE * d.nM; d.nwalk = d.nwin * d.W;
+    std::vector<int> lo, hi;
+    axis_windows(d.N + 1, d.nE, c->overlap_E, lo, hi);
+    d.wE = hi[0] - lo[0] + 1;
+    axis_windows(d.N + 1, d.nM, c->overlap_M, lo, hi);
+    d.wM = hi[0] - lo[0] + 1;
+    d.T = d.wE * d.wM;
+    d.tstride = ((long long)d.T + 63) / 64 * 64;
+    return d;
+}
+
+Layout layout_of(const Dims &d)
+{
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    const size_t B = (size_t)d.N + 1;
+    L.st = take(sizeof(DevState));
+    L.rect = take(sizeof(int4) * d.nwin);
+    L.active = take(sizeof(int32_t) * d.nwin);
+    L.spins = take(sizeof(uint32_t) * (size_t)d.nwords * d.nwalk);
+    L.we = take(sizeof(int32_t) * d.nwalk);
+    L.wm = take(sizeof(int32_t) * d.nwalk);
+    L.wt = take(sizeof(unsigned long long) * d.nwalk);
+    L.wflat = take(sizeof(int32_t) * d.nwalk);
+    L.lng = take(8 * (size_t)d.nwalk * d.tstride);
+    L.H = take(4 * (size_t)d.nwalk * d.tstride);
+    L.piece = take(8 * (size_t)d.nwin * d.tstride);
+    L.off = take(8 * (size_t)d.nwalk);
+    L.GE = take(8 * (size_t)d.nwin * d.wE);
+    L.eshift = take(8 * (size_t)d.nwin);
+    L.efrom = take(4 * (size_t)d.nwin);
+    L.eto = take(4 * (size_t)d.nwin);
+    L.ematch = take(4 * (size_t)d.nM * (d.nE > 1 ? d.nE - 1 : 1));
+    L.rowok = take(4 * (size_t)d.nM);
+    L.F = take(8 * (size_t)d.nM * B);
+    L.mshift = take(8 * (size_t)d.nM);
+    L.mfrom = take(4 * (size_t)d.nM);
+    L.mto = take(4 * (size_t)d.nM);
+    L.mmatch = take(4 * (size_t)(d.nM > 1 ? d.nM - 1 : 1));
+    L.J = take(std::max(8 * B * B, (size_t)d.nwalk * d.N));
+    L.red = take(8 * 2048);
+    L.marg = take(8 * B);
+    L.gbuf = take(8 * 2 * B * (size_t)d.nM);
+    L.fail = take(4);
+    L.total = o;
+    return L;
+}
+
+int max_pairs_of(const Dims &d)
+{
+    int best = 0;
+    for (int phase = 0; phase < 4; ++phase) {
+        const int axis = phase >> 1, parity = phase & 1;
+        const int nA = axis == 0 ? d.nE : d.nM, nO = axis == 0 ? d.nM : d.nE;
+        const int per = (nA - parity) / 2;
+        best = std::max(best, per > 0 ? per * nO : 0);
+    }
+    return best;
+}
+
+int sync(rewl_t *h)
+{
+    CK(h, cudaStreamSynchronize(h->stream));
+    return REWL_OK;
+}
+
+int read_state(rewl_t *h, DevState *ds)
+{
+    CK(h, cudaMemcpyAsync(ds, h->p.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (ds->error & ERR_OVERFLOW) return fail(h, REWL_E_OVERFLOW, "histogram entry above INT32_MAX");
+    return REWL_OK;
+}
+
+unsigned long long trials_of(rewl_t *h)
+{
+    unsigned long long t = 0;
+    if (h->first_active < 0) return 0;
+    if (cudaMemcpy(&t, h->p.wt + h->first_active, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    return t;
+}
+
+void fill_status(rewl_t *h, const DevState &ds, rewl_status *s)
+{
+    if (!s) return;
+    std::memset(s, 0, sizeof(*s));
+    s->iteration = ds.iter;
+    s->done = ds.done;
+    s->lnf = ds.lnf;
+    s->cycles = ds.cycle;
+    s->trials = trials_of(h);
+    s->exch_attempts = ds.exch_attempts;
+    s->exch_accepts = ds.exch_accepts;
+    s->n_flat = ds.nflat_last;
+    s->n_walkers = h->p.n_active_walkers;
+    s->error = ds.error;
+}
+
+// One cycle's kernels: sample, exchange, [flat check], counters, [H reset].
+cudaError_t queue_cycle(rewl_t *h, bool check)
+{
+    cudaError_t e;
+    if ((e = launch_sweep(h->p, h->cfg.exchange_interval, h->wpb, h->stream)) != cudaSuccess) return e;
+    if ((e = launch_exchange(h->p, h->max_pairs, h->stream)) != cudaSuccess) return e;
+    if (check && (e = launch_flat(h->p, h->stream)) != cudaSuccess) return e;
+    if ((e = launch_decide(h->p, DECIDE_XSTEP | DECIDE_CYCLE | (check ? DECIDE_CHECK : 0), h->stream)) != cudaSuccess) return e;
+    if (check && (e = launch_reset(h->p, h->stream)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+int build_graph(rewl_t *h)
+{
+    if (h->graph_ok || h->stream == nullptr) return REWL_OK;
+    cudaGraph_t g;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t qe = cudaSuccess;
+    for (int c = 0; c < h->cfg.check_every && qe == cudaSuccess; ++c)
+        qe = queue_cycle(h, c == h->cfg.check_every - 1);
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+    if (qe != cudaSuccess) return fail(h, REWL_E_CUDA, "queue during capture: %s", cudaGetErrorString(qe));
+    if (ce != cudaSuccess) return fail(h, REWL_E_CUDA, "capture: %s", cudaGetErrorString(ce));
+    cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return fail(h, REWL_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+    h->graph_ok = true;
+    return REWL_OK;
+}
+
+// Queues n cycles: whole check blocks through the graph, the rest eagerly.
+int queue_cycles(rewl_t *h, unsigned long long n)
+{
+    const unsigned long long ce = (unsigned long long)h->cfg.check_every;
+    while (n > 0) {
+        if (h->host_cycle % ce == 0 && n >= ce && h->stream != nullptr) {
+            int rc = build_graph(h);
+            if (rc) return rc;
+            CK(h, cudaGraphLaunch(h->graph, h->stream));
+            h->host_cycle += ce;
+            n -= ce;
+        } else {
+            const bool check = (h->host_cycle + 1) % ce == 0;
+            CK(h, queue_cycle(h, check));
+            h->host_cycle += 1;
+            n -= 1;
+        }
+    }
+    return REWL_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- ABI ----
+
+extern "C" int rewl_workspace_size(const rewl_config *cfg, size_t *bytes)
+{
+    const char *why = nullptr;
+    int rc = check_config(cfg, &why);
+    if (rc) return fail(nullptr, rc, "%s", why);
+    if (!bytes) return fail(nullptr, REWL_E_INVALID, "null bytes");
+    *bytes = layout_of(dims_of(cfg)).total;
+    return REWL_OK;
+}
+
+extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_workspace,
+                           size_t workspace_bytes, void *stream, rewl_t **out)
+{
+    const char *why = nullptr;
+    int rc = check_config(cfg, &why);
+    if (rc) return fail(nullptr, rc, "%s", why);
+    if (!out || !d_workspace) return fail(nullptr, REWL_E_INVALID, "null output or workspace");
+    if (((uintptr_t)d_workspace & 255u) != 0) return fail(nullptr, REWL_E_INVALID, "workspace not 256-byte aligned");
+    const Dims d = dims_of(cfg);
+    const Layout lay = layout_of(d);
+    if (workspace_bytes < lay.total)
+        return fail(nullptr, REWL_E_CAPACITY, "workspace %zu bytes < %zu needed", workspace_bytes, lay.total);
+
+    rewl_t *h = new (std::nothrow) rewl_t();
+    if (!h) return fail(nullptr, REWL_E_INVALID, "out of host memory");
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)stream;
+    h->err[0] = 0;
+    h->host_cycle = 0;
+    h->wpb = cfg->walkers_per_block;
+    h->graph_ok = false;
+    h->max_pairs = max_pairs_of(d);
+
+    char *base = (char *)d_workspace;
+    Params &p = h->p;
+    p.L = d.L; p.N = d.N; p.wpr = d.wpr; p.nwords = d.nwords;
+    p.nE = d.nE; p.nM = d.nM; p.W = d.W; p.nwin = d.nwin; p.nwalk = d.nwalk;
+    p.wE = d.wE; p.wM = d.wM; p.T = d.T; p.tstride = d.tstride;
+    p.precision = cfg->precision;
+    p.sampler = cfg->sampler;
+    // stage the tables in shared memory when a warp's share stays small
+    p.smt = 0;
+    p.key0 = (uint32_t)cfg->seed; p.key1 = (uint32_t)(cfg->seed >> 32);
+    p.divL = (uint32_t)((0x100000000ull + (unsigned long long)d.L - 1) / (unsigned long long)d.L);
+    p.lnf_final = cfg->lnf_final; p.lnf_factor = cfg->lnf_factor;
+    p.flat_q = (long long)std::llround(cfg->flatness * 1e6);
+    p.drive_budget = cfg->drive_budget;
+    p.rect = (const int4 *)(base + lay.rect);
+    p.active = (const int32_t *)(base + lay.active);
+    p.spins = (uint32_t *)(base + lay.spins);
+    p.we = (int32_t *)(base + lay.we);
+    p.wm = (int32_t *)(base + lay.wm);
+    p.wt = (unsigned long long *)(base + lay.wt);
+    p.wflat = (int32_t *)(base + lay.wflat);
+    p.lng = (double *)(base + lay.lng);
+    p.lng2 = (float2 *)(base + lay.lng);
+    p.H = (int32_t *)(base + lay.H);
+    p.st = (DevState *)(base + lay.st);
+    JoinScratch &j = h->j;
+    j.piece = (double *)(base + lay.piece);
+    j.off = (double *)(base + lay.off);
+    j.GE = (double *)(base + lay.GE);
+    j.eshift = (double *)(base + lay.eshift);
+    j.efrom = (int32_t *)(base + lay.efrom);
+    j.eto = (int32_t *)(base + lay.eto);
+    j.ematch = (int32_t *)(base + lay.ematch);
+    j.rowok = (int32_t *)(base + lay.rowok);
+    j.F = (double *)(base + lay.F);
+    j.mshift = (double *)(base + lay.mshift);
+    j.mfrom = (int32_t *)(base + lay.mfrom);
+    j.mto = (int32_t *)(base + lay.mto);
+    j.mmatch = (int32_t *)(base + lay.mmatch);
+    j.J = (double *)(base + lay.J);
+    j.red = (double *)(base + lay.red);
+    j.marg = (double *)(base + lay.marg);
+    j.gbuf = (double *)(base + lay.gbuf);
+    h->d_fail = (int32_t *)(base + lay.fail);
+    h->d_stage = (uint8_t *)(base + lay.J);
+
+    // Geometry on the host (integer setup), then uploaded.
+    std::vector<int> elo, ehi, mlo, mhi;
+    axis_windows(d.N + 1, d.nE, cfg->overlap_E, elo, ehi);
+    axis_windows(d.N + 1, d.nM, cfg->overlap_M, mlo, mhi);
+    std::vector<int4> rect(d.nwin);
+    std::vector<int32_t> active(d.nwin, 0);
+    int n_active = 0;
+    for (int b = 0; b < d.nM; ++b)
+        for (int a = 0; a < d.nE; ++a) {
+            const int win = b * d.nE + a;
+            rect[win] = make_int4(elo[a], ehi[a], mlo[b], mhi[b]);
+            bool any = false;
+            for (int e = elo[a]; e <= ehi[a] && !any; ++e)
+                for (int m = mlo[b]; m <= mhi[b] && !any; ++m) any = bin_can_hold(d.L, e, m);
+            active[win] = any ? 1 : 0;
+            n_active += any ? 1 : 0;
+        }
+    p.n_active_walkers = n_active * d.W;
+    // lanes per walker: a whole warp while walkers are few, packed groups when
+    // the walkers alone can fill the GPU
+    if (cfg->lanes_per_walker) p.group = cfg->lanes_per_walker;
+    else p.group = p.n_active_walkers <= 1216 ? 32 : (p.n_active_walkers <= 2432 ? 16 : 8);
+    p.smt = (p.sampler == REWL_SAMPLER_WARP &&
+             tree_smem_per_warp(p, true) * (size_t)(32 / p.group) <= 100 * 1024) ? 1 : 0;
+    h->first_active = -1;
+    for (int win = 0; win < d.nwin && h->first_active < 0; ++win)
+        if (active[win]) h->first_active = win * d.W;
+
+    auto bail = [&](int code) { rewl_destroy(h); return code; };
+    DevState ds;
+    std::memset(&ds, 0, sizeof(ds));
+    ds.lnf = cfg->lnf_init;
+    cudaError_t ce;
+#define CKB(call)                                                                              \
+    do {                                                                                       \
+        ce = (call);                                                                           \
+        if (ce != cudaSuccess) {                                                               \
+            fail(nullptr, REWL_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(ce));        \
+            return bail(REWL_E_CUDA);                                                          \
+        }                                                                                      \
+    } while (0)
+    CKB(cudaMemcpyAsync(p.st, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream));
+    CKB(cudaMemcpyAsync((void *)p.rect, rect.data(), sizeof(int4) * d.nwin, cudaMemcpyHostToDevice, h->stream));
+    CKB(cudaMemcpyAsync((void *)p.active, active.data(), sizeof(int32_t) * d.nwin, cudaMemcpyHostToDevice, h->stream));
+    // Tables: ln g = 0, H = -1 (never visited).
+    CKB(cudaMemsetAsync(p.lng, 0, 8 * (size_t)d.nwalk * d.tstride, h->stream));
+    CKB(cudaMemsetAsync(p.H, 0xFF, 4 * (size_t)d.nwalk * d.tstride, h->stream));
+    CKB(cudaMemsetAsync(h->d_fail, 0, 4, h->stream));
+    const uint8_t *d_bytes = nullptr;
+    if (host_init_spins) {
+        CKB(cudaMemcpyAsync(h->d_stage, host_init_spins, (size_t)d.nwalk * d.N, cudaMemcpyHostToDevice, h->stream));
+        d_bytes = h->d_stage;
+    }
+    CKB(launch_init(p, d_bytes, h->stream));
+    CKB(launch_drive(p, h->d_fail, h->stream));
+    int32_t failed = 0;
+    CKB(cudaMemcpyAsync(&failed, h->d_fail, 4, cudaMemcpyDeviceToHost, h->stream));
+    CKB(cudaStreamSynchronize(h->stream));
+#undef CKB
+    if (failed) {
+        fail(nullptr, REWL_E_UNREACHABLE, "a walker could not reach its window within %llu steps",
+             (unsigned long long)cfg->drive_budget);
+        return bail(REWL_E_UNREACHABLE);
+    }
+    *out = h;
+    return REWL_OK;
+}
+
+extern "C" int rewl_run_cycles(rewl_t *h, uint64_t n_cycles, rewl_status *status)
+{
+    if (!h) return REWL_E_INVALID;
+    int rc = queue_cycles(h, n_cycles);
+    if (rc) return rc;
+    DevState ds;
+    rc = read_state(h, &ds);
+    if (rc) return rc;
+    fill_status(h, ds, status);
+    return REWL_OK;
+}
+
+extern "C" int rewl_enqueue_cycle(rewl_t *h, int parts)
+{
+    if (!h || parts < 1 || parts > 3) return fail(h, REWL_E_INVALID, "bad parts %d", parts);
+    if (parts & REWL_PART_SAMPLE) CK(h, launch_sweep(h->p, h->cfg.exchange_interval, h->wpb, h->stream));
+    if (parts & REWL_PART_REST) {
+        const bool check = (h->host_cycle + 1) % (unsigned long long)h->cfg.check_every == 0;
+        CK(h, launch_exchange(h->p, h->max_pairs, h->stream));
+        if (check) CK(h, launch_flat(h->p, h->stream));
+        CK(h, launch_decide(h->p, DECIDE_XSTEP | DECIDE_CYCLE | (check ? DECIDE_CHECK : 0), h->stream));
+        if (check) CK(h, launch_reset(h->p, h->stream));
+        h->host_cycle += 1;
+    }
+    return REWL_OK;
+}
+
+extern "C" int rewl_run_iteration(rewl_t *h, uint64_t max_cycles, rewl_status *status)
+{
+    if (!h) return REWL_E_INVALID;
+    DevState ds;
+    int rc = read_state(h, &ds);
+    if (rc) return rc;
+    const int it0 = ds.iter;
+    if (ds.done) { fill_status(h, ds, status); return REWL_OK; }
+    uint64_t ran = 0;
+    const uint64_t ce = (uint64_t)h->cfg.check_every;
+    while (ran < max_cycles) {
+        // up to the next check boundary
+        uint64_t n = ce - (h->host_cycle % ce);
+        if (n > max_cycles - ran) n = max_cycles - ran;
+        rc = queue_cycles(h, n);
+        if (rc) return rc;
+        ran += n;
+        rc = read_state(h, &ds);
+        if (rc) return rc;
+        if (ds.done || ds.iter != it0) { fill_status(h, ds, status); return REWL_OK; }
+    }
+    fill_status(h, ds, status);
+    return fail(h, REWL_E_BUDGET, "no iteration ended within %llu cycles", (unsigned long long)max_cycles);
+}
+
+extern "C" int rewl_sweep(rewl_t *h, uint64_t n_trials)
+{
+    if (!h) return REWL_E_INVALID;
+    CK(h, launch_sweep(h->p, n_trials, h->wpb, h->stream));
+    DevState ds;
+    return read_state(h, &ds);
+}
+
+extern "C" int rewl_exchange(rewl_t *h)
+{
+    if (!h) return REWL_E_INVALID;
+    CK(h, launch_exchange(h->p, h->max_pairs, h->stream));
+    CK(h, launch_decide(h->p, DECIDE_XSTEP, h->stream));
+    return sync(h);
+}
+
+extern "C" int rewl_check(rewl_t *h, int32_t *all_flat)
+{
+    if (!h) return REWL_E_INVALID;
+    CK(h, launch_flat(h->p, h->stream));
+    CK(h, launch_decide(h->p, DECIDE_CHECK, h->stream));
+    CK(h, launch_reset(h->p, h->stream));
+    DevState ds;
+    int rc = read_state(h, &ds);
+    if (rc) return rc;
+    if (all_flat) *all_flat = ds.advanced;
+    return REWL_OK;
+}
+
+extern "C" int rewl_get_status(rewl_t *h, rewl_status *status)
+{
+    if (!h || !status) return REWL_E_INVALID;
+    DevState ds;
+    int rc = read_state(h, &ds);
+    if (rc) return rc;
+    fill_status(h, ds, status);
+    return REWL_OK;
+}
+
+extern "C" int rewl_get_windows(rewl_t *h, int32_t *host_out, size_t capacity)
+{
+    if (!h || !host_out) return REWL_E_INVALID;
+    const int n = h->p.nwin;
+    if (capacity < (size_t)n * 5) return fail(h, REWL_E_CAPACITY, "need %d entries", n * 5);
+    std::vector<int4> rect(n);
+    std::vector<int32_t> act(n);
+    CK(h, cudaMemcpyAsync(rect.data(), h->p.rect, sizeof(int4) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(act.data(), h->p.active, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < n; ++k) {
+        host_out[5 * k + 0] = rect[k].x; host_out[5 * k + 1] = rect[k].y;
+        host_out[5 * k + 2] = rect[k].z; host_out[5 * k + 3] = rect[k].w;
+        host_out[5 * k + 4] = act[k];
+    }
+    return REWL_OK;
+}
+
+extern "C" int rewl_get_walkers(rewl_t *h, int64_t *host_state, uint8_t *host_spins)
+{
+    if (!h) return REWL_E_INVALID;
+    const Params &p = h->p;
+    std::vector<int32_t> e(p.nwalk), m(p.nwalk), f(p.nwalk);
+    std::vector<unsigned long long> t(p.nwalk);
+    CK(h, cudaMemcpyAsync(e.data(), p.we, 4 * (size_t)p.nwalk, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(m.data(), p.wm, 4 * (size_t)p.nwalk, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(f.data(), p.wflat, 4 * (size_t)p.nwalk, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(t.data(), p.wt, 8 * (size_t)p.nwalk, cudaMemcpyDeviceToHost, h->stream));
+    std::vector<uint32_t> words;
+    if (host_spins) {
+        words.resize((size_t)p.nwords * p.nwalk);
+        CK(h, cudaMemcpyAsync(words.data(), p.spins, 4 * words.size(), cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int w = 0; w < p.nwalk; ++w) {
+        if (host_state) {
+            host_state[4 * w + 0] = e[w]; host_state[4 * w + 1] = m[w];
+            host_state[4 * w + 2] = (int64_t)t[w]; host_state[4 * w + 3] = f[w];
+        }
+        if (host_spins)
+            for (int i = 0; i < p.L; ++i)
+                for (int jj = 0; jj < p.L; ++jj) {
+                    const uint32_t wd = words[(size_t)(i * p.wpr + (jj >> 5)) * p.nwalk + w];
+                    host_spins[(size_t)w * p.N + i * p.L + jj] = (uint8_t)((wd >> (jj & 31)) & 1u);
+                }
+    }
+    return REWL_OK;
+}
+
+extern "C" int rewl_get_tables(rewl_t *h, double *host_lng, int32_t *host_H, size_t capacity)
+{
+    if (!h) return REWL_E_INVALID;
+    const Params &p = h->p;
+    const size_t n = (size_t)p.nwalk * p.T;
+    if (capacity < n) return fail(h, REWL_E_CAPACITY, "need %zu entries", n);
+    if (host_lng) {
+        if (p.precision == REWL_FP64) {
+            CK(h, cudaMemcpy2DAsync(host_lng, 8 * (size_t)p.T, p.lng, 8 * (size_t)p.tstride, 8 * (size_t)p.T,
+                                    p.nwalk, cudaMemcpyDeviceToHost, h->stream));
+        } else {
+            std::vector<float2> tmp(n);
+            CK(h, cudaMemcpy2DAsync(tmp.data(), 8 * (size_t)p.T, p.lng2, 8 * (size_t)p.tstride, 8 * (size_t)p.T,
+                                    p.nwalk, cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            for (size_t i = 0; i < n; ++i) host_lng[i] = (double)tmp[i].x + (double)tmp[i].y;
+        }
+    }
+    if (host_H)
+        CK(h, cudaMemcpy2DAsync(host_H, 4 * (size_t)p.T, p.H, 4 * (size_t)p.tstride, 4 * (size_t)p.T, p.nwalk,
+                                cudaMemcpyDeviceToHost, h->stream));
+    return sync(h);
+}
+
+extern "C" int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t *host_H, size_t count)
+{
+    if (!h) return REWL_E_INVALID;
+    const Params &p = h->p;
+    const size_t n = (size_t)p.nwalk * p.T;
+    if (count != n) return fail(h, REWL_E_CAPACITY, "need exactly %zu entries", n);
+    if (host_lng) {
+        if (p.precision == REWL_FP64) {
+            CK(h, cudaMemcpy2DAsync(p.lng, 8 * (size_t)p.tstride, host_lng, 8 * (size_t)p.T, 8 * (size_t)p.T,
+                                    p.nwalk, cudaMemcpyHostToDevice, h->stream));
+        } else {
+            std::vector<float2> tmp(n);
+            for (size_t i = 0; i < n; ++i) {
+                const float hi = (float)host_lng[i];
+                tmp[i] = make_float2(hi, (float)(host_lng[i] - (double)hi));
+            }
+            CK(h, cudaMemcpy2DAsync(p.lng2, 8 * (size_t)p.tstride, tmp.data(), 8 * (size_t)p.T, 8 * (size_t)p.T,
+                                    p.nwalk, cudaMemcpyHostToDevice, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        }
+    }
+    if (host_H)
+        CK(h, cudaMemcpy2DAsync(p.H, 4 * (size_t)p.tstride, host_H, 4 * (size_t)p.T, 4 * (size_t)p.T, p.nwalk,
+                                cudaMemcpyHostToDevice, h->stream));
+    return sync(h);
+}
+
+extern "C" int rewl_get_lng(rewl_t *h, int what, double *host_out, size_t capacity, size_t *needed,
+                            int32_t *host_ematch, int32_t *host_mmatch)
+{
+    if (!h) return REWL_E_INVALID;
+    const Params &p = h->p;
+    const size_t B = (size_t)p.N + 1;
+    size_t n;
+    if (what == REWL_LNG_JOINED) n = B * B;
+    else if (what == REWL_LNG_MARGINAL_E) n = B;
+    else return fail(h, REWL_E_INVALID, "unknown output kind %d", what);
+    if (needed) *needed = n;
+    if (!host_out || capacity < n) return fail(h, REWL_E_CAPACITY, "need %zu entries", n);
+    CK(h, cudaMemsetAsync(&p.st->join_error, 0, sizeof(int32_t), h->stream));
+    CK(h, launch_join(p, h->j, h->stream));
+    if (what == REWL_LNG_MARGINAL_E) CK(h, launch_marginal_e(p, h->j, h->stream));
+    DevState ds;
+    int rc = read_state(h, &ds);
+    if (rc) return rc;
+    if (ds.join_error) return fail(h, REWL_E_JOIN, "join failed (code %d): adjacent pieces share no visited bins", ds.join_error);
+    CK(h, cudaMemcpyAsync(host_out, what == REWL_LNG_JOINED ? h->j.J : h->j.marg, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+    if (host_ematch)
+        CK(h, cudaMemcpyAsync(host_ematch, h->j.ematch, 4 * (size_t)p.nM * (p.nE > 1 ? p.nE - 1 : 1),
+                              cudaMemcpyDeviceToHost, h->stream));
+    if (host_mmatch)
+        CK(h, cudaMemcpyAsync(host_mmatch, h->j.mmatch, 4 * (size_t)(p.nM > 1 ? p.nM - 1 : 1),
+                              cudaMemcpyDeviceToHost, h->stream));
+    return sync(h);
+}
+
+extern "C" const char *rewl_last_error(const rewl_t *h)
+{
+    if (!h) return g_create_err[0] ? g_create_err : g_noerr;
+    return h->err;
+}
+
+extern "C" int rewl_destroy(rewl_t *h)
+{
+    if (!h) return REWL_OK;
+    if (h->graph_ok) cudaGraphExecDestroy(h->graph);
+    delete h;
+    return REWL_OK;
+}
+
+extern "C" int rewl_philox(const uint32_t *d_ctr, const uint32_t *key, uint32_t *d_out, uint64_t n, void *stream)
+{
+    if (!key || (n && (!d_ctr || !d_out))) return fail(nullptr, REWL_E_INVALID, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_philox(d_ctr, key[0], key[1], d_out, n, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(nullptr, REWL_E_CUDA, "philox: %s", cudaGetErrorString(e));
+    return REWL_OK;
+}

@@ -1,0 +1,131 @@
+// Internal declarations of librewl (device path of two-dimensional
+// replica-exchange Wang-Landau sampling, arXiv:1508.02748).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "rewl.h"
+
+namespace rewl {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): two 32x32->64 products
+// per round on counter words 0 and 2, high halves folded into the other words
+// with the round key, key advanced by the two Weyl increments, ten rounds.
+struct u32x4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u32x4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = 0xD2511F53u * c0, ah = __umulhi(0xD2511F53u, c0);
+        const uint32_t b = 0xCD9E8D57u * c2, bh = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = bh ^ c1 ^ k0;
+        const uint32_t n2 = ah ^ c3 ^ k1;
+        c0 = n0; c1 = b; c2 = n2; c3 = a;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Stream tags of the counter's last word (one per kind of draw).
+enum : uint32_t { TAG_INIT = 1, TAG_DRIVE = 2, TAG_TRIAL = 3, TAG_PERM = 4, TAG_EXCH = 5 };
+
+// Scalars of a run that live in device memory (part of the workspace).
+struct DevState {
+    double lnf;                       // ln f of the current iteration
+    unsigned long long cycle;         // cycles run
+    unsigned long long xstep;         // exchange sweeps run (phase = xstep mod 4)
+    unsigned long long exch_attempts;
+    unsigned long long exch_accepts;
+    int32_t iter;                     // completed iterations
+    int32_t done;                     // final iteration flat
+    int32_t nflat;                    // walkers found flat by the running check
+    int32_t nflat_last;               // result of the last check
+    int32_t advanced;                 // the last check ended an iteration
+    int32_t error;                    // device error bits (ERR_*)
+    int32_t join_error;
+    int32_t pad;
+};
+
+enum : int32_t { ERR_OVERFLOW = 1, ERR_UNREACHABLE = 2 };
+
+// Everything a kernel needs, passed by value.
+struct Params {
+    int L, N;
+    int wpr;          // 32-bit words per lattice row
+    int nwords;       // words per lattice = L * wpr
+    int nE, nM, W;    // window grid, walkers per window
+    int nwin, nwalk;
+    int wE, wM;       // window extent in e and m (all windows equal)
+    int T;            // bins per window = wE * wM
+    long long tstride;// table entries per walker (T rounded up to 64)
+    int n_active_walkers;
+    int precision;
+    int sampler;      // REWL_SAMPLER_WARP or REWL_SAMPLER_THREAD
+    int smt;          // warp sampler: tables staged in shared memory
+    int group;        // warp sampler: lanes per walker
+    uint32_t key0, key1;
+    uint32_t divL;    // ceil(2^32 / L): site / L = umulhi(site, divL) for site < N
+    double lnf_final, lnf_factor;
+    long long flat_q; // round(flatness * 1e6)
+    uint64_t drive_budget;
+
+    const int4 *rect;       // per window: e0, e1, m0, m1
+    const int32_t *active;  // per window: 1 if it can hold a configuration
+
+    uint32_t *spins;  // nwords x nwalk, word-major: word k of walker w at k * nwalk + w
+    int32_t *we, *wm; // bins of each walker's configuration
+    unsigned long long *wt;  // trials done per walker
+    int32_t *wflat;   // last flatness verdict
+    double *lng;      // REWL_FP64: nwalk x tstride
+    float2 *lng2;     // REWL_F32X2: nwalk x tstride (hi, lo)
+    int32_t *H;       // nwalk x tstride, -1 = never visited
+    DevState *st;
+};
+
+// Join scratch (device pointers inside the workspace).
+struct JoinScratch {
+    double *piece;    // nwin x tstride merged ln g per window
+    double *off;      // nwalk: alignment offset of each walker to walker 0 of its window
+    double *GE;       // nwin x wE: E marginal of each piece (Eq. 3)
+    double *eshift;   // nwin: shift of each piece within its row
+    int32_t *efrom, *eto;   // nwin: e range [from, to) each piece covers in its row
+    int32_t *ematch;  // nM x max(1, nE-1)
+    int32_t *rowok;   // nM
+    double *F;        // nM x (N+1): M marginal of each row
+    double *mshift;   // nM
+    int32_t *mfrom, *mto;   // nM
+    int32_t *mmatch;  // max(1, nM-1)
+    double *J;        // (N+1) x (N+1) joined table
+    double *red;      // reduction scratch (>= 2 * 1024 doubles)
+    double *marg;     // N+1 marginal output
+    double *gbuf;     // nM x 2 x (N+1) work space of the E matching chains
+};
+
+// Kernel launchers (rewl_kernels.cu, rewl_join.cu); all return cudaError_t of the launch.
+cudaError_t launch_init(const Params &p, const uint8_t *d_init_bytes, cudaStream_t s);
+cudaError_t launch_drive(const Params &p, int32_t *d_fail, cudaStream_t s);
+cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int walkers_per_block, cudaStream_t s);
+cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int warps, bool smt, cudaStream_t s);
+size_t tree_smem_per_warp(const Params &p, bool smt);
+cudaError_t launch_exchange(const Params &p, int max_pairs, cudaStream_t s);
+cudaError_t launch_flat(const Params &p, cudaStream_t s);
+cudaError_t launch_decide(const Params &p, int flags, cudaStream_t s);
+cudaError_t launch_reset(const Params &p, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *d_ctr, uint32_t k0, uint32_t k1, uint32_t *d_out,
+                          uint64_t n, cudaStream_t s);
+cudaError_t launch_tables_to_double(const Params &p, double *d_out, cudaStream_t s);
+cudaError_t launch_tables_from_double(const Params &p, const double *d_in, cudaStream_t s);
+cudaError_t launch_join(const Params &p, const JoinScratch &j, cudaStream_t s);
+cudaError_t launch_marginal_e(const Params &p, const JoinScratch &j, cudaStream_t s);
+
+enum : int { DECIDE_XSTEP = 1, DECIDE_CYCLE = 2, DECIDE_CHECK = 4 };
+
+}  // namespace rewl

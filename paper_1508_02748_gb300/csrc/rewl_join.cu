@@ -1,0 +1,329 @@
+// Final merge, join and normalisation of librewl, all in FP64 on the device
+// (arXiv:1508.02748, Sec. 2, Eqs. 3-4):
+//   1. each window's walkers are merged: every walker is shifted by the mean,
+//      over the bins all walkers of the window visited, of its difference to
+//      walker 0; each bin is the mean over the walkers that visited it;
+//   2. within each row of windows (same M range), pieces are joined along E:
+//      g(E) = sum_M g(E,M) (Eq. 3) of each piece, beta(E) = d ln g / dE as the
+//      forward difference over one bin (dE = 4), E_mat = the overlap bin with
+//      minimal |beta_i - beta_j| (lowest on ties, never below the previous
+//      matching point), piece j rescaled to agree with piece i at E_mat, and
+//      piece i used for E < E_mat, piece j for E >= E_mat (Eq. 4);
+//   3. the rows are joined along M by the same rule on g(M) = sum_E g(E,M)
+//      (dM = 2), "one at a time" as Sec. 2 prescribes for both axes split;
+//   4. the joined table is shifted so that sum g = 2^N.
+// Loops that the sums depend on run in a fixed order (one thread per output
+// element), so results differ from a serial evaluation only by the rounding
+// of exp/log and of the final parallel normalisation sum.
+#include <math.h>
+
+#include "rewl_internal.cuh"
+
+namespace rewl {
+
+namespace {
+
+__device__ __forceinline__ double lng_at(const Params &p, size_t i)
+{
+    if (p.precision == REWL_FP64) return p.lng[i];
+    const float2 v = p.lng2[i];
+    return (double)v.x + (double)v.y;
+}
+
+__device__ __forceinline__ bool all_seen(const Params &p, int win, int bin)
+{
+    for (int k = 0; k < p.W; ++k)
+        if (p.H[(size_t)(win * p.W + k) * p.tstride + bin] < 0) return false;
+    return true;
+}
+
+// Serial log-sum-exp in index order: max, then sum of exp(v - max) over the
+// finite entries.
+template <typename F>
+__device__ double lse_serial(int n, F get)
+{
+    double mx = -INFINITY;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, get(i));
+    if (mx == -INFINITY) return -INFINITY;
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double v = get(i);
+        if (v != -INFINITY) acc += exp(v - mx);
+    }
+    return mx + log(acc);
+}
+
+// Matching point (Eq. 4) between marginals Ga, Gb over [lo, hi], p >= floor.
+__device__ int match_point(const double *Ga, const double *Gb, int lo, int hi, int floor_p, double step)
+{
+    int best = -1;
+    double bestd = INFINITY;
+    const int start = lo > floor_p ? lo : floor_p;
+    for (int q = start; q + 1 <= hi; ++q) {
+        if (Ga[q] == -INFINITY || Ga[q + 1] == -INFINITY) continue;
+        if (Gb[q] == -INFINITY || Gb[q + 1] == -INFINITY) continue;
+        const double ba = (Ga[q + 1] - Ga[q]) / step;
+        const double bb = (Gb[q + 1] - Gb[q]) / step;
+        const double d = fabs(ba - bb);
+        if (d < bestd) { bestd = d; best = q; }
+    }
+    if (best >= 0) return best;
+    for (int q = start; q <= hi; ++q)
+        if (Ga[q] != -INFINITY && Gb[q] != -INFINITY) return q;
+    return -1;
+}
+
+}  // namespace
+
+// 1a. Offsets: one thread per (window, walker k >= 1), bins in order.
+__global__ void k_merge_off(Params p, JoinScratch j)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= p.nwalk) return;
+    const int win = idx / p.W, k = idx % p.W;
+    if (!p.active[win]) return;
+    if (k == 0) { j.off[idx] = 0.0; return; }
+    const size_t b0 = (size_t)(win * p.W) * p.tstride, bk = (size_t)idx * p.tstride;
+    double acc = 0.0;
+    long long common = 0;
+    for (int i = 0; i < p.T; ++i) {
+        if (!all_seen(p, win, i)) continue;
+        acc += lng_at(p, bk + i) - lng_at(p, b0 + i);
+        ++common;
+    }
+    if (common == 0) { atomicExch(&p.st->join_error, 1); j.off[idx] = 0.0; return; }
+    j.off[idx] = acc / (double)common;
+}
+
+// 1b. Merged piece: one thread per (window, bin), walkers in order.
+__global__ void k_merge(Params p, JoinScratch j)
+{
+    const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (idx >= (size_t)p.nwin * p.T) return;
+    const int win = (int)(idx / p.T), bin = (int)(idx % p.T);
+    double *out = j.piece + (size_t)win * p.tstride + bin;
+    if (!p.active[win]) { *out = -INFINITY; return; }
+    double acc = 0.0;
+    int cnt = 0;
+    for (int k = 0; k < p.W; ++k) {
+        const size_t q = (size_t)(win * p.W + k) * p.tstride + bin;
+        if (p.H[q] < 0) continue;
+        acc += lng_at(p, q) - j.off[win * p.W + k];
+        ++cnt;
+    }
+    *out = cnt ? acc / (double)cnt : -INFINITY;
+}
+
+// 2a. E marginal of each piece over its M range (Eq. 3).
+__global__ void k_marg_piece(Params p, JoinScratch j)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= p.nwin * p.wE) return;
+    const int win = idx / p.wE, el = idx % p.wE;
+    const double *row = j.piece + (size_t)win * p.tstride + (size_t)el * p.wM;
+    j.GE[idx] = p.active[win] ? lse_serial(p.wM, [&](int i) { return row[i]; }) : -INFINITY;
+}
+
+// 2b. One thread per row b: chain of E matching points along the row.
+__global__ void k_match_e(Params p, JoinScratch j, double *gbuf)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.nM) return;
+    const int nE = p.nE, B = p.N + 1;
+    double *Ga = gbuf + (size_t)b * 2 * B, *Gb = Ga + B;
+    for (int a = 0; a < nE; ++a) {
+        j.efrom[b * nE + a] = 0; j.eto[b * nE + a] = 0; j.eshift[b * nE + a] = 0.0;
+        if (a < nE - 1) j.ematch[b * (nE - 1) + a] = -1;
+    }
+    if (nE == 1) j.ematch[b] = -1;
+    int first = -1, last = -1;
+    for (int a = 0; a < nE; ++a)
+        if (p.active[b * nE + a]) { if (first < 0) first = a; last = a; }
+    j.rowok[b] = first >= 0;
+    if (first < 0) return;
+    for (int a = first; a <= last; ++a)
+        if (!p.active[b * nE + a]) { atomicExch(&p.st->join_error, 2); return; }
+    double shift = 0.0;
+    int from = p.rect[b * nE + first].x;
+    for (int a = first; a <= last; ++a) {
+        const int A = b * nE + a;
+        const int4 RA = p.rect[A];
+        int to;
+        double next_shift = 0.0;
+        if (a < last) {
+            const int4 RB = p.rect[A + 1];
+            for (int e = 0; e < B; ++e) { Ga[e] = -INFINITY; Gb[e] = -INFINITY; }
+            for (int e = RA.x; e <= RA.y; ++e) Ga[e] = j.GE[A * p.wE + (e - RA.x)];
+            for (int e = RB.x; e <= RB.y; ++e) Gb[e] = j.GE[(A + 1) * p.wE + (e - RB.x)];
+            const int q = match_point(Ga, Gb, RB.x, RA.y, from, 4.0);
+            if (q < 0) { atomicExch(&p.st->join_error, 3); return; }
+            j.ematch[b * (nE - 1) + a] = q;
+            next_shift = shift + (Ga[q] - Gb[q]);
+            to = q;
+        } else {
+            to = RA.y + 1;
+        }
+        j.efrom[A] = from; j.eto[A] = to; j.eshift[A] = shift;
+        shift = next_shift;
+        from = to;
+    }
+}
+
+// Value of row b at (e, m): the piece covering e in that row, shifted.
+__device__ __forceinline__ double row_value(const Params &p, const JoinScratch &j, int b, int e, int m)
+{
+    for (int a = 0; a < p.nE; ++a) {
+        const int A = b * p.nE + a;
+        if (e >= j.efrom[A] && e < j.eto[A]) {
+            const int4 R = p.rect[A];
+            if (m < R.z || m > R.w) return -INFINITY;
+            const double v = j.piece[(size_t)A * p.tstride + (size_t)(e - R.x) * p.wM + (m - R.z)];
+            return v == -INFINITY ? v : v + j.eshift[A];
+        }
+    }
+    return -INFINITY;
+}
+
+// 3a. M marginal of each row: F_b(m) = ln sum_E g_b(E, m), e ascending.
+__global__ void k_marg_row(Params p, JoinScratch j)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int B = p.N + 1;
+    if (idx >= p.nM * B) return;
+    const int b = idx / B, m = idx % B;
+    if (!j.rowok[b]) { j.F[idx] = -INFINITY; return; }
+    j.F[idx] = lse_serial(B, [&](int e) { return row_value(p, j, b, e, m); });
+}
+
+// 3b. Single thread: chain of M matching points over the rows.
+__global__ void k_match_m(Params p, JoinScratch j)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int nM = p.nM, nE = p.nE, B = p.N + 1;
+    for (int b = 0; b < nM; ++b) { j.mfrom[b] = 0; j.mto[b] = 0; j.mshift[b] = 0.0; }
+    for (int b = 0; b < (nM > 1 ? nM - 1 : 1); ++b) j.mmatch[b] = -1;
+    int first = -1, last = -1;
+    for (int b = 0; b < nM; ++b) if (j.rowok[b]) { if (first < 0) first = b; last = b; }
+    if (first < 0) { atomicExch(&p.st->join_error, 4); return; }
+    for (int b = first; b <= last; ++b) if (!j.rowok[b]) { atomicExch(&p.st->join_error, 5); return; }
+    double shift = 0.0;
+    int from = p.rect[first * nE].z;
+    for (int b = first; b <= last; ++b) {
+        int to;
+        double next_shift = 0.0;
+        if (b < last) {
+            const double *Ga = j.F + (size_t)b * B, *Gb = j.F + (size_t)(b + 1) * B;
+            const int lo = p.rect[(b + 1) * nE].z, hi = p.rect[b * nE].w;
+            const int q = match_point(Ga, Gb, lo, hi, from, 2.0);
+            if (q < 0) { atomicExch(&p.st->join_error, 6); return; }
+            j.mmatch[b] = q;
+            next_shift = shift + (Ga[q] - Gb[q]);
+            to = q;
+        } else {
+            to = p.rect[b * nE].w + 1;
+        }
+        j.mfrom[b] = from; j.mto[b] = to; j.mshift[b] = shift;
+        shift = next_shift;
+        from = to;
+    }
+}
+
+// 3c. Assemble the joined table.
+__global__ void k_assemble(Params p, JoinScratch j)
+{
+    const int B = p.N + 1;
+    const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (idx >= (size_t)B * B) return;
+    const int e = (int)(idx / B), m = (int)(idx % B);
+    double v = -INFINITY;
+    for (int b = 0; b < p.nM; ++b) {
+        if (m >= j.mfrom[b] && m < j.mto[b]) {
+            const double r = row_value(p, j, b, e, m);
+            v = r == -INFINITY ? r : r + j.mshift[b];
+            break;
+        }
+    }
+    j.J[idx] = v;
+}
+
+// 4. Normalisation: max, then sum of exp(v - max), block partials in red[].
+__global__ void k_red_max(const double *v, size_t n, double *red)
+{
+    double mx = -INFINITY;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        mx = fmax(mx, v[i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    __shared__ double s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, s[k]);
+        red[blockIdx.x] = mx;
+    }
+}
+
+__global__ void k_red_sumexp(const double *v, size_t n, const double *red_max, int nblk_max, double *red)
+{
+    double mx = -INFINITY;
+    for (int k = 0; k < nblk_max; ++k) mx = fmax(mx, red_max[k]);
+    double acc = 0.0;
+    if (mx != -INFINITY)
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+            if (v[i] != -INFINITY) acc += exp(v[i] - mx);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    __shared__ double s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) acc += s[k];
+        red[blockIdx.x] = acc;
+    }
+}
+
+__global__ void k_normalise(double *v, size_t n, const double *red_max, const double *red_sum, int nblk, int N)
+{
+    double mx = -INFINITY, acc = 0.0;
+    for (int k = 0; k < nblk; ++k) mx = fmax(mx, red_max[k]);
+    for (int k = 0; k < nblk; ++k) acc += red_sum[k];
+    const double lz = mx + log(acc);
+    const double c = (double)N * log(2.0) - lz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (v[i] != -INFINITY) v[i] += c;
+}
+
+cudaError_t launch_join(const Params &p, const JoinScratch &j, cudaStream_t s)
+{
+    const int B = p.N + 1;
+    k_merge_off<<<(p.nwalk + 127) / 128, 128, 0, s>>>(p, j);
+    const size_t nb = (size_t)p.nwin * p.T;
+    k_merge<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(p, j);
+    k_marg_piece<<<(p.nwin * p.wE + 127) / 128, 128, 0, s>>>(p, j);
+    k_match_e<<<(p.nM + 31) / 32, 32, 0, s>>>(p, j, j.gbuf);
+    k_marg_row<<<(p.nM * B + 127) / 128, 128, 0, s>>>(p, j);
+    k_match_m<<<1, 1, 0, s>>>(p, j);
+    const size_t nJ = (size_t)B * B;
+    k_assemble<<<(unsigned)((nJ + 255) / 256), 256, 0, s>>>(p, j);
+    const int nblk = 512;
+    k_red_max<<<nblk, 256, 0, s>>>(j.J, nJ, j.red);
+    k_red_sumexp<<<nblk, 256, 0, s>>>(j.J, nJ, j.red, nblk, j.red + nblk);
+    k_normalise<<<nblk, 256, 0, s>>>(j.J, nJ, j.red, j.red + nblk, nblk, p.N);
+    return cudaGetLastError();
+}
+
+// Eq. 3 on the joined table: ln sum_m g(e, m), m ascending.
+__global__ void k_marg_out(Params p, JoinScratch j)
+{
+    const int B = p.N + 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B) return;
+    const double *row = j.J + (size_t)e * B;
+    j.marg[e] = lse_serial(B, [&](int i) { return row[i]; });
+}
+
+cudaError_t launch_marginal_e(const Params &p, const JoinScratch &j, cudaStream_t s)
+{
+    k_marg_out<<<(p.N + 1 + 127) / 128, 128, 0, s>>>(p, j);
+    return cudaGetLastError();
+}
+
+}  // namespace rewl

@@ -1,0 +1,279 @@
+"""Python binding of librewl (include/rewl.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; PyTorch provides
+the device workspace (one uint8 tensor) and the stream.  There is no CPU
+fallback: constructing :class:`REWL` without the built library or without a
+CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librewl.so")
+
+REWL_OK = 0
+ERRORS = {-1: "INVALID", -2: "CUDA", -3: "TIMEOUT", -4: "UNREACHABLE", -5: "OVERFLOW",
+          -6: "BUDGET", -7: "JOIN", -8: "CAPACITY"}
+FP64, F32X2 = 0, 1
+PART_SAMPLE, PART_REST = 1, 2
+SAMPLER_WARP, SAMPLER_THREAD = 0, 1
+LNG_JOINED, LNG_MARGINAL_E = 0, 1
+
+
+class REWLError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"REWL_E_{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rewl_config(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("L", ctypes.c_int32),
+                ("n_win_E", ctypes.c_int32), ("n_win_M", ctypes.c_int32),
+                ("overlap_E", ctypes.c_double), ("overlap_M", ctypes.c_double),
+                ("walkers_per_window", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("lnf_init", ctypes.c_double), ("lnf_final", ctypes.c_double),
+                ("lnf_factor", ctypes.c_double), ("flatness", ctypes.c_double),
+                ("exchange_interval", ctypes.c_uint64), ("check_every", ctypes.c_int32),
+                ("walkers_per_block", ctypes.c_int32), ("sampler", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32),
+                ("seed", ctypes.c_uint64),
+                ("drive_budget", ctypes.c_uint64)]
+
+
+class rewl_status(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int32), ("done", ctypes.c_int32), ("lnf", ctypes.c_double),
+                ("cycles", ctypes.c_uint64), ("trials", ctypes.c_uint64),
+                ("exch_attempts", ctypes.c_uint64), ("exch_accepts", ctypes.c_uint64),
+                ("n_flat", ctypes.c_int32), ("n_walkers", ctypes.c_int32),
+                ("error", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# Every symbol include/rewl.h declares, with its ctypes signature.
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "rewl_workspace_size": (ctypes.c_int, [ctypes.POINTER(rewl_config), ctypes.POINTER(ctypes.c_size_t)]),
+    "rewl_create": (ctypes.c_int, [ctypes.POINTER(rewl_config), _P, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "rewl_run_cycles": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(rewl_status)]),
+    "rewl_run_iteration": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(rewl_status)]),
+    "rewl_enqueue_cycle": (ctypes.c_int, [_P, ctypes.c_int]),
+    "rewl_sweep": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "rewl_exchange": (ctypes.c_int, [_P]),
+    "rewl_check": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "rewl_get_status": (ctypes.c_int, [_P, ctypes.POINTER(rewl_status)]),
+    "rewl_get_windows": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "rewl_get_walkers": (ctypes.c_int, [_P, _P, _P]),
+    "rewl_get_tables": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t]),
+    "rewl_set_tables": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t]),
+    "rewl_get_lng": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _P, _P]),
+    "rewl_last_error": (ctypes.c_char_p, [_P]),
+    "rewl_destroy": (ctypes.c_int, [_P]),
+    "rewl_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Loads librewl.so (built by ``paper_1508_02748_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"librewl.so not built ({p}); run "
+                                   "`python -m paper_1508_02748_gb300.build`")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, handle=None):
+    if rc != REWL_OK:
+        msg = load_library().rewl_last_error(handle)
+        raise REWLError(rc, msg.decode() if msg else "")
+
+
+@dataclass
+class Config:
+    L: int
+    n_win_E: int = 1
+    n_win_M: int = 1
+    overlap_E: float = 0.75
+    overlap_M: float = 0.75
+    walkers_per_window: int = 1
+    precision: int = FP64
+    lnf_init: float = 1.0
+    lnf_final: float = 1e-6
+    lnf_factor: float = 0.5
+    flatness: float = 0.8
+    exchange_interval: int = 10000
+    check_every: int = 1
+    walkers_per_block: int = 0
+    sampler: int = 0
+    lanes_per_walker: int = 0
+    seed: int = 1
+    drive_budget: int = 10_000_000
+
+    def to_c(self) -> rewl_config:
+        c = rewl_config()
+        c.struct_size = ctypes.sizeof(rewl_config)
+        for name, _ in rewl_config._fields_[1:]:
+            setattr(c, name, getattr(self, name))
+        return c
+
+    @classmethod
+    def from_workload(cls, w, replicate: int = 0, **kw) -> "Config":
+        d = dict(L=w.L, n_win_E=w.n_win_E, n_win_M=w.n_win_M, overlap_E=w.overlap_E,
+                 overlap_M=w.overlap_M, walkers_per_window=w.walkers_per_window,
+                 lnf_init=w.lnf_init, lnf_final=w.lnf_final, lnf_factor=w.lnf_factor,
+                 flatness=w.flatness, exchange_interval=w.exchange_interval,
+                 check_every=w.check_every, seed=w.seed(replicate))
+        d.update(kw)
+        return cls(**d)
+
+
+def _status_dict(s: rewl_status) -> dict:
+    return {name: getattr(s, name) for name, _ in rewl_status._fields_ if name != "reserved"}
+
+
+class REWL:
+    """One REWL run on a CUDA device (handle of include/rewl.h)."""
+
+    def __init__(self, cfg: Config, init_spins: np.ndarray | None = None, device: str = "cuda:0",
+                 stream=None):
+        import torch
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("REWL needs a CUDA device")
+        self.cfg = cfg
+        self._c = cfg.to_c()
+        self.device = torch.device(device)
+        nbytes = ctypes.c_size_t(0)
+        _check(lib.rewl_workspace_size(ctypes.byref(self._c), ctypes.byref(nbytes)))
+        self.workspace_bytes = int(nbytes.value)
+        self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        sp = None
+        if init_spins is not None:
+            sp = np.ascontiguousarray(init_spins, dtype=np.uint8)
+        h = ctypes.c_void_p(0)
+        with torch.cuda.device(self.device):
+            rc = lib.rewl_create(ctypes.byref(self._c), None if sp is None else sp.ctypes.data,
+                                 ctypes.c_void_p(self.workspace.data_ptr()), self.workspace_bytes,
+                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _check(rc, None)
+        self._h = h
+        self.N = cfg.L * cfg.L
+        self.n_windows = cfg.n_win_E * cfg.n_win_M
+        self.n_walkers = self.n_windows * cfg.walkers_per_window
+
+    # ---------------------------------------------------------------- run --
+    def run_cycles(self, n: int) -> dict:
+        s = rewl_status()
+        _check(load_library().rewl_run_cycles(self._h, n, ctypes.byref(s)), self._h)
+        return _status_dict(s)
+
+    def run_iteration(self, max_cycles: int) -> tuple[bool, dict]:
+        """Runs until an iteration ends; (False, status) if max_cycles ran first."""
+        s = rewl_status()
+        rc = load_library().rewl_run_iteration(self._h, max_cycles, ctypes.byref(s))
+        if rc == -6:
+            return False, _status_dict(s)
+        _check(rc, self._h)
+        return True, _status_dict(s)
+
+    def enqueue_cycle(self, parts: int = PART_SAMPLE | PART_REST):
+        """Queues one cycle (or its SAMPLE / REST part) on self.stream without waiting."""
+        _check(load_library().rewl_enqueue_cycle(self._h, parts), self._h)
+
+    def sweep(self, n_trials: int):
+        _check(load_library().rewl_sweep(self._h, n_trials), self._h)
+
+    def exchange(self):
+        _check(load_library().rewl_exchange(self._h), self._h)
+
+    def check(self) -> bool:
+        f = ctypes.c_int32(0)
+        _check(load_library().rewl_check(self._h, ctypes.byref(f)), self._h)
+        return bool(f.value)
+
+    def status(self) -> dict:
+        s = rewl_status()
+        _check(load_library().rewl_get_status(self._h, ctypes.byref(s)), self._h)
+        return _status_dict(s)
+
+    # -------------------------------------------------------------- state --
+    def windows(self) -> np.ndarray:
+        out = np.zeros((self.n_windows, 5), dtype=np.int32)
+        _check(load_library().rewl_get_windows(self._h, out.ctypes.data, out.size), self._h)
+        return out
+
+    def walkers(self, spins: bool = True):
+        st = np.zeros((self.n_walkers, 4), dtype=np.int64)
+        sp = np.zeros((self.n_walkers, self.N), dtype=np.uint8) if spins else None
+        _check(load_library().rewl_get_walkers(self._h, st.ctypes.data,
+                                               None if sp is None else sp.ctypes.data), self._h)
+        return st, sp
+
+    def _bins(self) -> int:
+        w = self.windows()[0]
+        return int((w[1] - w[0] + 1) * (w[3] - w[2] + 1))
+
+    def tables(self):
+        n = self.n_walkers * self._bins()
+        lng = np.zeros(n, dtype=np.float64)
+        H = np.zeros(n, dtype=np.int32)
+        _check(load_library().rewl_get_tables(self._h, lng.ctypes.data, H.ctypes.data, n), self._h)
+        return lng, H
+
+    def set_tables(self, lng: np.ndarray, H: np.ndarray):
+        lng = np.ascontiguousarray(lng, dtype=np.float64)
+        H = np.ascontiguousarray(H, dtype=np.int32)
+        _check(load_library().rewl_set_tables(self._h, lng.ctypes.data, H.ctypes.data, lng.size), self._h)
+
+    def lng(self, what: int = LNG_JOINED, matches: bool = False):
+        B = self.N + 1
+        n = B * B if what == LNG_JOINED else B
+        out = np.zeros(n, dtype=np.float64)
+        need = ctypes.c_size_t(0)
+        nE, nM = self.cfg.n_win_E, self.cfg.n_win_M
+        em = np.zeros(max(1, nM * max(1, nE - 1)), dtype=np.int32)
+        mm = np.zeros(max(1, nM - 1), dtype=np.int32)
+        _check(load_library().rewl_get_lng(self._h, what, out.ctypes.data, n, ctypes.byref(need),
+                                           em.ctypes.data, mm.ctypes.data), self._h)
+        out = out.reshape(B, B) if what == LNG_JOINED else out
+        return (out, em, mm) if matches else out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().rewl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def philox(counters, key) -> "object":
+    """Device Philox4x32-10 of n counters (torch uint32-compatible int32 tensor n x 4 on CUDA)."""
+    import torch
+    c = counters.contiguous()
+    out = torch.empty_like(c)
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    s = torch.cuda.current_stream(c.device)
+    _check(load_library().rewl_philox(ctypes.c_void_p(c.data_ptr()), k.ctypes.data,
+                                      ctypes.c_void_p(out.data_ptr()), c.shape[0],
+                                      ctypes.c_void_p(s.cuda_stream)))
+    return out
