@@ -121,13 +121,13 @@ int check_config(const rewl_config *c, const char **why)
     if (!(c->overlap_E >= 0.0 && c->overlap_E < 1.0 && c->overlap_M >= 0.0 && c->overlap_M < 1.0)) { *why = "overlap must be in [0, 1)"; return REWL_E_INVALID; }
     if (c->walkers_per_window < 1 || c->walkers_per_window > 1024) { *why = "walkers_per_window must be in [1, 1024]"; return REWL_E_INVALID; }
     if (c->precision != REWL_FP64 && c->precision != REWL_F32X2) { *why = "unknown precision"; return REWL_E_INVALID; }
-    if (c->precision != REWL_FP64) { *why = "REWL_F32X2 sampling is not built yet"; return REWL_E_INVALID; }
     if (!(c->lnf_init > 0.0 && c->lnf_final > 0.0 && c->lnf_factor > 0.0 && c->lnf_factor < 1.0)) { *why = "bad ln f schedule"; return REWL_E_INVALID; }
     if (!(c->flatness > 0.0 && c->flatness <= 1.0)) { *why = "flatness must be in (0, 1]"; return REWL_E_INVALID; }
     if (c->exchange_interval < 1) { *why = "exchange_interval must be >= 1"; return REWL_E_INVALID; }
     if (c->check_every < 1) { *why = "check_every must be >= 1"; return REWL_E_INVALID; }
     if (c->walkers_per_block < 0 || c->walkers_per_block > 128) { *why = "walkers_per_block must be in [0, 128]"; return REWL_E_INVALID; }
     if (c->sampler != REWL_SAMPLER_WARP && c->sampler != REWL_SAMPLER_THREAD) { *why = "unknown sampler"; return REWL_E_INVALID; }
+    if (c->sampler == REWL_SAMPLER_THREAD && c->precision != REWL_FP64) { *why = "the thread sampler supports REWL_FP64 only"; return REWL_E_INVALID; }
     if (c->sampler == REWL_SAMPLER_WARP && c->walkers_per_block > 8) { *why = "warp sampler: walkers_per_block (warps per block) must be in [0, 8]"; return REWL_E_INVALID; }
     if (c->lanes_per_walker != 0 && c->lanes_per_walker != 8 && c->lanes_per_walker != 16 && c->lanes_per_walker != 32) { *why = "lanes_per_walker must be 0, 8, 16 or 32"; return REWL_E_INVALID; }
     return REWL_OK;

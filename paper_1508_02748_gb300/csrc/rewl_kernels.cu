@@ -286,7 +286,15 @@ __global__ void __launch_bounds__(128) k_sweep_fp64(Params p, unsigned long long
 
 cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int wpb, cudaStream_t s)
 {
-    if (p.sampler == REWL_SAMPLER_WARP) return launch_sweep_tree(p, ntrials, p.group, wpb, p.smt != 0, s);
+    if (p.sampler == REWL_SAMPLER_WARP) {
+        while (ntrials > 0) {
+            const uint64_t n = ntrials > (1ull << 30) ? (1ull << 30) : ntrials;
+            const cudaError_t e = launch_sweep_tree(p, n, p.group, wpb, p.smt != 0, s);
+            if (e != cudaSuccess) return e;
+            ntrials -= n;
+        }
+        return cudaSuccess;
+    }
     if (wpb <= 0) wpb = 32;
     const int blocks = (p.nwalk + wpb - 1) / wpb;
     const size_t smem = (size_t)p.nwords * wpb * sizeof(uint32_t);

@@ -17,21 +17,24 @@
 //      and walks them to find its current bin and the bins visited;
 //   3. decides its own trial (Eq. 1) with the exact ln g values the sequential
 //      chain would see there: value(bin) = table(bin) + visits * ln f.
-// One ballot then follows the true path from the root; the leaf lane of that
-// path commits the DEPTH+1 trials (spin flips, the ln g / H updates of every
-// bin visited, the new current bin) and the group adopts its state.
+// One ballot gives the true path from the root.  The path and the trial
+// sites are then known to every lane, and lane k of the path knows the bin
+// the walker is in after trial t+k; after five shuffles, lane k commits
+// trial k: its spin flip, and the ln g / H update of its bin if that bin is
+// left in this step (first occurrence only, with all its visits).
 //
 // The outcome is the sequential chain itself, trial for trial:
 //   - random numbers are drawn per trial index from the TRIAL stream of
 //     Philox4x32-10, independent of the state (a ring of 128 trials per
 //     walker, refilled 64 at a time from the even trial at or below the
 //     launch's first trial);
-//   - table(bin) + visits * ln f is evaluated as fma(visits, ln f, table),
-//     the same number as the sequential additions whenever ln f = 2^-k (every
-//     partial sum is then exact);
+//   - table(bin) + visits * ln f is evaluated exactly: fma in double for
+//     REWL_FP64, a compensated (hi, lo) float sum for REWL_F32X2; both equal
+//     the sequential additions whenever ln f = 2^-k and the values stay
+//     within the exact range of the format;
 //   - decisions are screened in float with a margin that bounds the float
-//     rounding, and re-taken in double on near-ties, as in the one-thread
-//     sampler.
+//     rounding (|x - float(x)| < 2^-23 |x| for both table formats) and
+//     re-taken in double on near-ties.
 // The walker's current bin stays in registers (its table value at entry,
 // the visits since then) and is written back when the walker leaves it.
 #include "rewl_internal.cuh"
@@ -54,8 +57,14 @@ __device__ __forceinline__ float trunc_f(double x)
 
 __device__ __forceinline__ double unit_open_d(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
 
+// One buffered trial (16 bytes, one shared-memory vector load).  Everything
+// about a trial that does not depend on the walker's state is computed when
+// the ring is refilled: the site and its four periodic neighbours, and ln u.
 struct RingEntry {
-    uint32_t ij;   // row << 16 | column of the site
+    uint32_t a;    // register lattice: the 6-bit indices of the site and of its up,
+                   //   down, left and right neighbours at bits 0, 6, 12, 18, 24;
+                   // shared lattice: row | col << 8 | up-row << 16 | down-row << 24
+    uint32_t b;    // shared lattice: left-col | right-col << 8
     uint32_t xu;   // acceptance word
     float lnu;     // ln u in float
 };
@@ -65,17 +74,63 @@ struct TreeShape {
     static constexpr int DEPTH = G == 32 ? 4 : G == 16 ? 3 : G == 8 ? 2 : 1;
 };
 
+// (hi, lo) + x for a float x, compensated (Knuth's two-sum, then a fast
+// renormalisation): exact while the result has at most ~48 significant bits
+// and every addend is a multiple of the finest ln f.
+__device__ __forceinline__ float2 add2(float2 a, float x)
+{
+    const float s = __fadd_rn(a.x, x);
+    const float bb = __fsub_rn(s, a.x);
+    const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    const float l2 = __fadd_rn(a.y, err);
+    const float h2 = __fadd_rn(s, l2);
+    const float l3 = __fsub_rn(l2, __fsub_rn(h2, s));
+    return make_float2(h2, l3);
+}
+
+// Table value types.  Val: the value of one bin as kept in registers.
+template <int PREC>
+struct Tab;
+
+template <>
+struct Tab<REWL_FP64> {
+    using Elem = double;
+    using Val = double;
+    __device__ static Val load(const Elem *t, int i) { return t[i]; }
+    __device__ static float approx(Val v) { return trunc_f(v); }       // |err| < 2^-23 |v|
+    __device__ static double exact(Val v) { return v; }
+    // v + n * lnf (exact for the dyadic schedule)
+    __device__ static Val add(Val v, int n, double lnf, float) { return fma((double)n, lnf, v); }
+};
+
+template <>
+struct Tab<REWL_F32X2> {
+    using Elem = float2;
+    using Val = float2;
+    __device__ static Val load(const Elem *t, int i) { return t[i]; }
+    __device__ static float approx(Val v) { return v.x; }               // |err| <= 2^-24 |v|
+    __device__ static double exact(Val v) { return (double)v.x + (double)v.y; }
+    __device__ static Val add(Val v, int n, double, float lnf32) { return add2(v, __fmul_rn((float)n, lnf32)); }
+};
+
 }  // namespace
 
-template <int WPR, bool SMT, int G>
-__global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned long long ntrials, int smem_per_walker)
+// REG: the lattice (N <= 64 sites, bit i*L + j) is held in a 64-bit register
+// by every lane; otherwise it lives in shared memory, one 32-bit word per row
+// (two for L > 32).
+template <int WPR, bool SMT, int G, int PREC, bool REG>
+__global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, int smem_per_walker)
 {
+    using TB = Tab<PREC>;
+    using Elem = typename TB::Elem;
+    using Val = typename TB::Val;
     constexpr int DEPTH = TreeShape<G>::DEPTH;
     constexpr int GPW = 32 / G;   // walkers per warp
+    constexpr unsigned GBITS = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gl = lane & (G - 1), grp = lane / G;
-    const unsigned gmask = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << (grp * G));
+    const unsigned gmask = GBITS << (grp * G);
     const int slot = wid * GPW + grp;   // walker slot within the block
     const int w = blockIdx.x * ((blockDim.x >> 5) * GPW) + slot;
     if (w >= p.nwalk) return;
@@ -86,287 +141,300 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned long long
     uint32_t *lat = reinterpret_cast<uint32_t *>(base + RING * sizeof(RingEntry));
     const int L = p.L, nwords = L * WPR;
     const int T = p.T;
-    double *gl_tab = p.lng + (size_t)w * p.tstride;
+    Elem *g_tab = (PREC == REWL_FP64) ? reinterpret_cast<Elem *>(p.lng) : reinterpret_cast<Elem *>(p.lng2);
+    g_tab += (size_t)w * p.tstride;
     int32_t *gH = p.H + (size_t)w * p.tstride;
-    double *tl;
+    Elem *tl;
     int32_t *tH;
     if (SMT) {
-        tl = reinterpret_cast<double *>(base + RING * sizeof(RingEntry) + ((nwords * 4 + 15) & ~15));
+        tl = reinterpret_cast<Elem *>(base + RING * sizeof(RingEntry) + ((nwords * 4 + 15) & ~15));
         tH = reinterpret_cast<int32_t *>(tl + T);
-        for (int k = gl; k < T; k += G) { tl[k] = gl_tab[k]; tH[k] = gH[k]; }
+        for (int k = gl; k < T; k += G) { tl[k] = g_tab[k]; tH[k] = gH[k]; }
     } else {
-        tl = gl_tab;
+        tl = g_tab;
         tH = gH;
     }
-    for (int k = gl; k < nwords; k += G) lat[k] = p.spins[(size_t)k * p.nwalk + w];
+    unsigned long long lat64 = 0;
+    if (REG) {
+        for (int r = 0; r < L; ++r)
+            lat64 |= (unsigned long long)p.spins[(size_t)r * p.nwalk + w] << (r * L);
+    } else {
+        for (int k = gl; k < nwords; k += G) lat[k] = p.spins[(size_t)k * p.nwalk + w];
+    }
     __syncwarp(gmask);
 
     const int4 R = p.rect[w / p.W];
     const int wM = p.wM;
+    const unsigned spanE = (unsigned)(R.y - R.x), spanM = (unsigned)(R.w - R.z);
     const double lnf = p.st->lnf;
     const float lnf32 = trunc_f(lnf);
     const uint32_t N = (uint32_t)p.N;
     const uint32_t divL = p.divL;
 
-    // this lane's node of the tree
+    // this lane's node of the tree and the lanes holding its history's trials
     const int dl = 31 - __clz(gl + 1);
     const int hist = gl + 1 - (1 << dl);
+    int srck[DEPTH];
+    #pragma unroll
+    for (int k = 0; k < DEPTH; ++k) srck[k] = (1 << k) - 1 + (hist & ((1 << k) - 1));
 
     // committed state (uniform over the group)
     int e = p.we[w], m = p.wm[w];
     int ci = (e - R.x) * wM + (m - R.z);
-    double lbase = tl[ci];      // table value of the current bin when entered
-    int lq = 0;                 // ln f steps since lbase
-    int hq = 0;                 // visits of the current bin not yet in H
+    Val lbase = TB::load(tl, ci);   // table value of the current bin when entered
+    int lq = 0;                     // ln f steps since lbase
+    int hq = 0;                     // visits of the current bin not yet in H
     int hbase = tH[ci];
-    float base32 = trunc_f(lbase);
-    unsigned long long t = p.wt[w];
-    const unsigned long long tend = t + ntrials;
-    unsigned long long tfill = t & ~1ull;
+    float base32 = TB::approx(lbase);
+    const unsigned long long t0 = p.wt[w];
+    const unsigned r0 = (unsigned)t0 & (RING - 1);
+    unsigned u = 0;                 // trials done in this launch
+    unsigned ufill = 0;             // ring holds trials [t0 - (t0 & 1), t0 + ufill)
+    const unsigned long long c0 = t0 >> 1;   // first Philox call
+    unsigned cfill = 0;             // calls done
     int err = 0;
 
-    auto bit = [&](int r, int c) -> uint32_t {
-        const int q = (WPR == 1) ? 0 : (c >> 5);
-        return (lat[r * WPR + q] >> (c & 31)) & 1u;
-    };
-
-    while (t < tend) {
+    while (u < ntrials) {
         // ---- refill the ring: 32 Philox calls = 64 trials
-        if (tfill < t + 32) {
+        if (ufill < u + 32) {
             #pragma unroll
             for (int r = 0; r < 32 / G; ++r) {
-                const unsigned long long c = (tfill >> 1) + (unsigned long long)(gl + r * G);
+                const unsigned long long c = c0 + cfill + (unsigned)(gl + r * G);
                 const u32x4 x = philox10((uint32_t)c, (uint32_t)(c >> 32), (uint32_t)w, TAG_TRIAL, p.key0, p.key1);
                 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     const uint32_t xs = hh ? x.z : x.x, xu = hh ? x.w : x.y;
                     const uint32_t site = __umulhi(xs, N);
                     const uint32_t i = __umulhi(site, divL);
-                    const uint32_t jj = site - i * (uint32_t)L;
+                    const uint32_t j = site - i * (uint32_t)L;
+                    const uint32_t iu = i == 0 ? L - 1 : i - 1, id = i == (uint32_t)L - 1 ? 0 : i + 1;
+                    const uint32_t jl = j == 0 ? L - 1 : j - 1, jr = j == (uint32_t)L - 1 ? 0 : j + 1;
                     RingEntry en;
-                    en.ij = (i << 16) | jj;
+                    if (REG) {
+                        en.a = site | ((iu * L + j) << 6) | ((id * L + j) << 12) | ((i * L + jl) << 18) | ((i * L + jr) << 24);
+                        en.b = 0;
+                    } else {
+                        en.a = i | (j << 8) | (iu << 16) | (id << 24);
+                        en.b = jl | (jr << 8);
+                    }
                     en.xu = xu;
                     en.lnu = logf(__fmaf_rn(__uint2float_rn(xu), 0x1p-32f, 0x1p-33f));
-                    ring[(2 * c + hh) & (RING - 1)] = en;
+                    ring[(unsigned)(2 * c + hh) & (RING - 1)] = en;
                 }
             }
-            tfill += 64;
+            cfill += 32;
+            ufill = 2 * cfill - (unsigned)(t0 & 1ull);
             __syncwarp(gmask);
         }
         if (lq >= (1 << 22)) {       // keep the float screen's counts exact
-            lbase = fma((double)lq, lnf, lbase);
+            lbase = TB::add(lbase, lq, lnf, lnf32);
             lq = 0;
-            base32 = trunc_f(lbase);
+            base32 = TB::approx(lbase);
         }
-        const unsigned long long left = tend - t;
-        const int D = left > (unsigned long long)DEPTH ? DEPTH : (int)left - 1;
+        const unsigned left = ntrials - u;
+        const int D = left > (unsigned)DEPTH ? DEPTH : (int)left - 1;
+        const unsigned rb = r0 + u;
 
         // ---- 1. own trial under own history
-        const RingEntry me = ring[(t + dl) & (RING - 1)];
-        int sk[DEPTH];               // sites of the earlier trials
+        const RingEntry me = ring[(rb + dl) & (RING - 1)];
+        uint32_t sa[DEPTH + 1];      // site words of trials t .. t+DEPTH (uniform)
         #pragma unroll
-        for (int k = 0; k < DEPTH; ++k) sk[k] = (int)ring[(t + k) & (RING - 1)].ij;
-        const int si = (int)(me.ij >> 16), sj = (int)(me.ij & 0xFFFFu);
-        const int iu = si == 0 ? L - 1 : si - 1, id = si == L - 1 ? 0 : si + 1;
-        const int jl = sj == 0 ? L - 1 : sj - 1, jr = sj == L - 1 ? 0 : sj + 1;
-        uint32_t s = bit(si, sj), bu = bit(iu, sj), bd = bit(id, sj), bl = bit(si, jl), br = bit(si, jr);
-        #pragma unroll
-        for (int k = 0; k < DEPTH; ++k) {
-            if (k < dl && ((hist >> k) & 1)) {
-                const int fi = sk[k] >> 16, fj = sk[k] & 0xFFFF;
-                s ^= (fi == si && fj == sj);
-                bu ^= (fi == iu && fj == sj);
-                bd ^= (fi == id && fj == sj);
-                bl ^= (fi == si && fj == jl);
-                br ^= (fi == si && fj == jr);
+        for (int k = 0; k <= DEPTH; ++k) sa[k] = ring[(rb + k) & (RING - 1)].a;
+        uint32_t sbit, bu, bd, bl, br;
+        unsigned long long fm = 0;   // register lattice: sites flipped by the history
+        if (REG) {
+            #pragma unroll
+            for (int k = 0; k < DEPTH; ++k)
+                if (k < dl && ((hist >> k) & 1)) fm ^= 1ull << (sa[k] & 63u);   // a site may flip twice
+            const unsigned long long v = lat64 ^ fm;
+            sbit = (uint32_t)(v >> (me.a & 63u)) & 1u;
+            bu = (uint32_t)(v >> ((me.a >> 6) & 63u)) & 1u;
+            bd = (uint32_t)(v >> ((me.a >> 12) & 63u)) & 1u;
+            bl = (uint32_t)(v >> ((me.a >> 18) & 63u)) & 1u;
+            br = (uint32_t)(v >> ((me.a >> 24) & 63u)) & 1u;
+        } else {
+            const int i = me.a & 255, j = (me.a >> 8) & 255, iu = (me.a >> 16) & 255, id = me.a >> 24;
+            const int jl = me.b & 255, jr = (me.b >> 8) & 255;
+            const int qj = (WPR == 1) ? 0 : (j >> 5);
+            const uint32_t wc = lat[i * WPR + qj], wu = lat[iu * WPR + qj], wd = lat[id * WPR + qj];
+            sbit = (wc >> (j & 31)) & 1u;
+            bu = (wu >> (j & 31)) & 1u;
+            bd = (wd >> (j & 31)) & 1u;
+            bl = ((WPR == 1 ? wc : lat[i * WPR + (jl >> 5)]) >> (jl & 31)) & 1u;
+            br = ((WPR == 1 ? wc : lat[i * WPR + (jr >> 5)]) >> (jr & 31)) & 1u;
+            const uint32_t p_s = i | (j << 8), p_u = iu | (j << 8), p_d = id | (j << 8);
+            const uint32_t p_l = i | (jl << 8), p_r = i | (jr << 8);
+            #pragma unroll
+            for (int k = 0; k < DEPTH; ++k) {
+                if (k < dl && ((hist >> k) & 1)) {
+                    const uint32_t f = sa[k] & 0xFFFFu;
+                    sbit ^= (f == p_s);
+                    bu ^= (f == p_u);
+                    bd ^= (f == p_d);
+                    bl ^= (f == p_l);
+                    br ^= (f == p_r);
+                }
             }
         }
         const int nup = (int)(bu + bd + bl + br);
-        const int de_own = s ? nup - 2 : 2 - nup;
-        const int dm_own = s ? -1 : 1;
+        const int de_own = sbit ? nup - 2 : 2 - nup;
+        const int dm_own = sbit ? -1 : 1;
         const int pack = (de_own + 2) | ((dm_own + 1) << 3);
 
-        // ---- 2. earlier trials of the history: moves from their lanes
-        int ce = e, cm = m;
-        bool ok = dl <= D;
-        int vb[DEPTH];               // bin after each earlier trial
+        // ---- 2. the history's earlier trials: moves from the lanes that took them
+        // (a history that accepts a move out of the window is never the true
+        // path; its bins are clamped below only to keep its reads in bounds)
+        int ce = e, cm = m, cbin = ci;
+        int vb[DEPTH];               // bin after each earlier trial (-1 past the own depth)
         #pragma unroll
         for (int k = 0; k < DEPTH; ++k) {
-            const int src = (1 << k) - 1 + (hist & ((1 << k) - 1));
-            const int pk = __shfl_sync(gmask, pack, src, G);
-            vb[k] = -1;
-            if (k < dl) {
-                if ((hist >> k) & 1) {
-                    const int en_ = ce + (pk & 7) - 2, mn_ = cm + ((pk >> 3) & 3) - 1;
-                    if (en_ < R.x || en_ > R.y || mn_ < R.z || mn_ > R.w) ok = false;  // never accepted
-                    ce = en_;
-                    cm = mn_;
-                }
-                vb[k] = (ce - R.x) * wM + (cm - R.z);
+            const int pk = __shfl_sync(gmask, pack, srck[k], G);
+            if (k < dl && ((hist >> k) & 1)) {
+                const int de = (pk & 7) - 2, dm = ((pk >> 3) & 3) - 1;
+                ce += de;
+                cm += dm;
+                cbin += de * wM + dm;
             }
+            vb[k] = k < dl ? cbin : -1;
         }
 
         // ---- 3. decision of the own trial (Eq. 1)
         const int en_o = ce + de_own, mn_o = cm + dm_own;
-        int acc = 0;
-        if (ok && en_o >= R.x && en_o <= R.y && mn_o >= R.z && mn_o <= R.w) {
-            const int cb = (ce - R.x) * wM + (cm - R.z);
-            const int nbn = (en_o - R.x) * wM + (mn_o - R.z);
-            int vcur = 0, vnew = 0;
-            #pragma unroll
-            for (int k = 0; k < DEPTH; ++k) {
-                vcur += (vb[k] == cb);
-                vnew += (vb[k] == nbn);
-            }
-            const bool c0 = cb == ci, n0 = nbn == ci;
-            const double cbase = c0 ? lbase : tl[cb];
-            const double nbase = n0 ? lbase : tl[nbn];
-            const int ccnt = vcur + (c0 ? lq : 0), ncnt = vnew + (n0 ? lq : 0);
-            const float cb32 = c0 ? base32 : trunc_f(cbase);
-            const float nb32 = n0 ? base32 : trunc_f(nbase);
-            const float c32 = __fmaf_rn((float)ccnt, lnf32, cb32);
-            const float n32 = __fmaf_rn((float)ncnt, lnf32, nb32);
-            const float d32 = c32 - n32;
-            const float M = (fabsf(c32) + fabsf(n32) + fabsf(cb32) + fabsf(nb32) + fabsf(me.lnu)) * 0x1p-20f
-                          + 0x1p-20f;
-            if (me.lnu < d32 - M) {
-                acc = 1;
-            } else if (me.lnu > d32 + M) {
-                acc = 0;
-            } else {
-                const double delta = fma((double)ccnt, lnf, cbase) - fma((double)ncnt, lnf, nbase);
-                acc = (delta >= 0.0 || log(unit_open_d(me.xu)) < delta) ? 1 : 0;
-            }
+        const int nbin = cbin + de_own * wM + dm_own;
+        const bool live = dl <= D && (unsigned)(en_o - R.x) <= spanE && (unsigned)(mn_o - R.z) <= spanM;
+        const int cb = min(max(cbin, 0), T - 1), nb = min(max(nbin, 0), T - 1);
+        int vcur = 0, vnew = 0;
+        #pragma unroll
+        for (int k = 0; k < DEPTH; ++k) {
+            vcur += (vb[k] == cb);
+            vnew += (vb[k] == nb);
         }
+        const bool c0b = cb == ci, n0b = nb == ci;
+        const Val tc = TB::load(tl, cb), tn = TB::load(tl, nb);
+        const Val cbase = c0b ? lbase : tc;
+        const Val nbase = n0b ? lbase : tn;
+        const int ccnt = vcur + (c0b ? lq : 0), ncnt = vnew + (n0b ? lq : 0);
+        const float cb32 = c0b ? base32 : TB::approx(tc);
+        const float nb32 = n0b ? base32 : TB::approx(tn);
+        const float c32 = __fmaf_rn((float)ccnt, lnf32, cb32);
+        const float n32 = __fmaf_rn((float)ncnt, lnf32, nb32);
+        const float d32 = c32 - n32;
+        const float M = (fabsf(c32) + fabsf(n32) + fabsf(cb32) + fabsf(nb32) + fabsf(me.lnu)) * 0x1p-20f + 0x1p-20f;
+        int acc = (me.lnu < d32 - M) ? 1 : 0;
+        if (live && !acc && !(me.lnu > d32 + M)) {
+            const double delta = fma((double)ccnt, lnf, TB::exact(cbase)) - fma((double)ncnt, lnf, TB::exact(nbase));
+            acc = (delta >= 0.0 || log(unit_open_d(me.xu)) < delta) ? 1 : 0;
+        }
+        acc = live ? acc : 0;
+        const int after = acc ? nbin : cbin;   // bin after the own trial, under the own history
 
-        // ---- follow the true path
-        const unsigned bal = (__ballot_sync(gmask, acc) >> (grp * G)) & (G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u));
-        int path = 0;
+        // ---- follow the true path from the root
+        const unsigned bal = (__ballot_sync(gmask, acc) >> (grp * G)) & GBITS;
+        int path = 0, node = 0, leaf = 0;
         #pragma unroll
         for (int k = 0; k <= DEPTH; ++k) {
             if (k <= D) {
-                const int ln = (1 << k) - 1 + path;
-                path |= (int)((bal >> ln) & 1u) << k;
+                leaf = node;
+                const int b = (bal >> node) & 1u;
+                path |= b << k;
+                node += (1 + b) << k;
             }
         }
-        const int leaf = (1 << D) - 1 + (path & ((1 << D) - 1));
 
-        // ---- commit (leaf lane), then the group adopts the new state
-        int n_e = e, n_m = m, n_ci = ci, n_lq = lq, n_hq = hq, n_hb = hbase;
-        double n_lb = lbase;
-        if (gl == leaf) {
-            int fl[DEPTH + 1];
-            int vv[DEPTH + 1];
+        // ---- commit: lane k takes trial t+k of the path
+        const int pk_src = (1 << (gl & 31)) - 1 + (path & ((1 << (gl & 31)) - 1));
+        const int xs = __shfl_sync(gmask, after, gl <= D ? pk_src : 0, G);
+        const int X = gl <= D ? xs : -1 - gl;   // bin after trial t+gl (unique dummies past D)
+        const unsigned mm = (__match_any_sync(gmask, X) >> (grp * G)) & GBITS;
+        const int C = __shfl_sync(gmask, X, D, G);
+        const int cC = __popc(__shfl_sync(gmask, mm, D, G));
+        const bool b0_seen = ((__ballot_sync(gmask, X == ci) >> (grp * G)) & ((2u << D) - 1u)) != 0;
+        if (REG) {
+            // the path's flips: the leaf's history plus the leaf's own trial if accepted
+            const unsigned long long fl = fm ^ (acc ? (1ull << (me.a & 63u)) : 0ull);
+            lat64 ^= __shfl_sync(gmask, fl, leaf, G);
+        } else if (gl <= D && ((path >> gl) & 1)) {
+            uint32_t fs = sa[0];
             #pragma unroll
-            for (int k = 0; k < DEPTH; ++k) {
-                fl[k] = (k < D && ((path >> k) & 1)) ? sk[k] : -1;
-                vv[k] = k < D ? vb[k] : -1;
+            for (int k = 1; k <= DEPTH; ++k) if (gl == k) fs = sa[k];
+            const int fi = fs & 255, fj = (fs >> 8) & 255;
+            atomicXor(&lat[fi * WPR + ((WPR == 1) ? 0 : (fj >> 5))], 1u << (fj & 31));
+        }
+        // write-back of a bin the walker leaves in this step (all its visits)
+        {
+            const bool own = gl <= D && (__ffs(mm) - 1) == gl && X != C;
+            const bool entry_left = gl == G - 1 && C != ci && !b0_seen && hq > 0;
+            if (own || entry_left) {
+                const int Xw = own ? X : ci;
+                const bool isci = Xw == ci;
+                const int cnt = own ? __popc(mm) : 0;
+                const Val v0 = isci ? lbase : TB::load(tl, Xw);
+                const int h0 = isci ? hbase : tH[Xw];
+                const int nv = cnt + (isci ? lq : 0), nh = cnt + (isci ? hq : 0);
+                const long long hv = (long long)(h0 < 0 ? 0 : h0) + nh;
+                if (hv > 0x7FFFFFFFll) err = 1;
+                tl[Xw] = TB::add(v0, nv, lnf, lnf32);
+                tH[Xw] = (int32_t)hv;
             }
-            const bool a = (path >> D) & 1;
-            fl[DEPTH] = a ? (int)me.ij : -1;
-            const int fe = a ? en_o : ce, fm = a ? mn_o : cm;
-            const int C = (fe - R.x) * wM + (fm - R.z);
-            vv[DEPTH] = C;     // the visit of the last trial (slot DEPTH stands for trial D)
-            #pragma unroll
-            for (int k = 0; k <= DEPTH; ++k) {
-                if (fl[k] >= 0) {
-                    const int fi = fl[k] >> 16, fj = fl[k] & 0xFFFF;
-                    atomicXor(&lat[fi * WPR + ((WPR == 1) ? 0 : (fj >> 5))], 1u << (fj & 31));
-                }
-            }
-            // write back every bin visited in this step other than the final one
-            int cC = 0;
-            bool b0_seen = false;
-            #pragma unroll
-            for (int k = 0; k <= DEPTH; ++k) {
-                const int X = vv[k];
-                if (X < 0) continue;
-                cC += (X == C);
-                b0_seen |= (X == ci);
-                bool first = true;
-                int cnt = 0;
-                #pragma unroll
-                for (int k2 = 0; k2 <= DEPTH; ++k2) {
-                    if (k2 < k && vv[k2] == X) first = false;
-                    cnt += (vv[k2] == X);
-                }
-                if (first && X != C) {
-                    if (X == ci) {
-                        const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq + cnt;
-                        if (hv > 0x7FFFFFFFll) err = 1;
-                        tl[X] = fma((double)(lq + cnt), lnf, lbase);
-                        tH[X] = (int32_t)hv;
-                    } else {
-                        const int32_t h0 = tH[X];
-                        const long long hv = (long long)(h0 < 0 ? 0 : h0) + cnt;
-                        if (hv > 0x7FFFFFFFll) err = 1;
-                        tl[X] = fma((double)cnt, lnf, tl[X]);
-                        tH[X] = (int32_t)hv;
-                    }
-                }
-            }
-            if (C == ci) {
-                n_lq = lq + cC;
-                n_hq = hq + cC;
-            } else {
-                if (!b0_seen && hq > 0) {      // left the entry bin on the first trial
-                    const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
-                    if (hv > 0x7FFFFFFFll) err = 1;
-                    tl[ci] = fma((double)lq, lnf, lbase);
-                    tH[ci] = (int32_t)hv;
-                }
-                n_ci = C;
-                n_lb = tl[C];
-                n_hb = tH[C];
-                n_lq = cC;
-                n_hq = cC;
-            }
-            n_e = fe;
-            n_m = fm;
+        }
+        // the group adopts the state after the last trial
+        {
+            const int em_leaf = acc ? ((en_o << 16) | mn_o) : ((ce << 16) | cm);
+            const int em = __shfl_sync(gmask, em_leaf, leaf, G);
+            e = em >> 16;
+            m = em & 0xFFFF;
+        }
+        if (C == ci) {
+            lq += cC;
+            hq += cC;
+        } else {
+            lbase = TB::load(tl, C);
+            hbase = tH[C];
+            base32 = TB::approx(lbase);
+            ci = C;
+            lq = cC;
+            hq = cC;
         }
         __syncwarp(gmask);
-        e = __shfl_sync(gmask, n_e, leaf, G);
-        m = __shfl_sync(gmask, n_m, leaf, G);
-        const int new_ci = __shfl_sync(gmask, n_ci, leaf, G);
-        lq = __shfl_sync(gmask, n_lq, leaf, G);
-        hq = __shfl_sync(gmask, n_hq, leaf, G);
-        hbase = __shfl_sync(gmask, n_hb, leaf, G);
-        lbase = __shfl_sync(gmask, n_lb, leaf, G);
-        if (new_ci != ci) base32 = trunc_f(lbase);
-        ci = new_ci;
-        t += (unsigned long long)(D + 1);
+        u += (unsigned)(D + 1);
     }
 
     // ---- flush the current bin and the state
     if (gl == 0 && hq > 0) {
         const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
         if (hv > 0x7FFFFFFFll) err = 1;
-        tl[ci] = fma((double)lq, lnf, lbase);
+        tl[ci] = TB::add(lbase, lq, lnf, lnf32);
         tH[ci] = (int32_t)hv;
     }
     __syncwarp(gmask);
     if (SMT)
-        for (int k = gl; k < T; k += G) { gl_tab[k] = tl[k]; gH[k] = tH[k]; }
-    for (int k = gl; k < nwords; k += G) p.spins[(size_t)k * p.nwalk + w] = lat[k];
+        for (int k = gl; k < T; k += G) { g_tab[k] = tl[k]; gH[k] = tH[k]; }
+    if (REG) {
+        for (int r = gl; r < L; r += G)
+            p.spins[(size_t)r * p.nwalk + w] = (uint32_t)(lat64 >> (r * L)) & (uint32_t)((1ull << L) - 1);
+    } else {
+        for (int k = gl; k < nwords; k += G) p.spins[(size_t)k * p.nwalk + w] = lat[k];
+    }
     if (gl == 0) {
         p.we[w] = e;
         p.wm[w] = m;
-        p.wt[w] = t;
+        p.wt[w] = t0 + u;
     }
     err = __any_sync(gmask, err);
     if (gl == 0 && err) atomicOr(&p.st->error, ERR_OVERFLOW);
 }
 
 // Shared memory per walker: ring, lattice (16-byte padded) and, when staged,
-// the tables.
+// the tables (8-byte ln g entries in either format, 4-byte H).
 size_t tree_smem_per_warp(const Params &p, bool smt)
 {
     size_t b = RING * sizeof(RingEntry) + (((size_t)p.nwords * 4 + 15) & ~(size_t)15);
-    if (smt) b += (size_t)p.T * (sizeof(double) + sizeof(int32_t));
+    if (smt) b += (size_t)p.T * (8 + sizeof(int32_t));
     return (b + 15) & ~(size_t)15;
 }
 
-// group: lanes per walker (8, 16 or 32); warps: warps per block.
+// group: lanes per walker (8, 16 or 32); warps: warps per block.  One
+// launch runs fewer than 2^31 trials per walker (launch_sweep splits).
 cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int warps, bool smt, cudaStream_t s)
 {
     if (group != 8 && group != 16 && group != 32) group = 32;
@@ -382,19 +450,28 @@ cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int 
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        kern<<<blocks, threads, smem, s>>>(p, (unsigned long long)ntrials, (int)per);
+        kern<<<blocks, threads, smem, s>>>(p, (unsigned)ntrials, (int)per);
         return cudaGetLastError();
     };
-#define REWL_TREE_CASES(W_, S_)                                           \
-    if (group == 32) return go(k_sweep_tree<W_, S_, 32>);                 \
-    if (group == 16) return go(k_sweep_tree<W_, S_, 16>);                 \
-    return go(k_sweep_tree<W_, S_, 8>);
+#define REWL_TREE_G(W_, S_, P_)                                            \
+    if (p.N <= 64 && W_ == 1) {                                            \
+        if (group == 32) return go(k_sweep_tree<1, S_, 32, P_, true>);     \
+        if (group == 16) return go(k_sweep_tree<1, S_, 16, P_, true>);     \
+        return go(k_sweep_tree<1, S_, 8, P_, true>);                       \
+    }                                                                      \
+    if (group == 32) return go(k_sweep_tree<W_, S_, 32, P_, false>);       \
+    if (group == 16) return go(k_sweep_tree<W_, S_, 16, P_, false>);       \
+    return go(k_sweep_tree<W_, S_, 8, P_, false>);
+#define REWL_TREE_P(W_, S_)                                                \
+    if (p.precision == REWL_FP64) { REWL_TREE_G(W_, S_, REWL_FP64) }       \
+    else { REWL_TREE_G(W_, S_, REWL_F32X2) }
     if (p.wpr == 1) {
-        if (smt) { REWL_TREE_CASES(1, true) } else { REWL_TREE_CASES(1, false) }
+        if (smt) { REWL_TREE_P(1, true) } else { REWL_TREE_P(1, false) }
     } else {
-        if (smt) { REWL_TREE_CASES(2, true) } else { REWL_TREE_CASES(2, false) }
+        if (smt) { REWL_TREE_P(2, true) } else { REWL_TREE_P(2, false) }
     }
-#undef REWL_TREE_CASES
+#undef REWL_TREE_P
+#undef REWL_TREE_G
 }
 
 }  // namespace rewl

@@ -98,26 +98,27 @@ def test_host_init_spins(P):
 SAMPLERS = [0, 1]   # warp (tree speculation), thread
 
 
-@pytest.mark.parametrize("sampler,lanes", [(0, 32), (0, 16), (0, 8), (1, 0)])
+@pytest.mark.parametrize("sampler,lanes,prec", [(0, 32, 0), (0, 16, 1), (0, 8, 0), (0, 32, 1), (1, 0, 0)])
 @pytest.mark.parametrize("L", [4, 5, 6, 8, 24, 33, 48, 64])
-def test_sweep_bit_exact_single_window(P, L, sampler, lanes):
-    """Sec. 2 trial/update rule, one window over the full (E, M) range."""
+def test_sweep_bit_exact_single_window(P, L, sampler, lanes, prec):
+    """Sec. 2 trial/update rule, one window over the full (E, M) range; both
+    ln g formats (double, compensated float pair) follow the same chain."""
     o, g = _pair(P, L=L, walkers_per_window=3, seed=77 + L, exchange_interval=5000, sampler=sampler,
-                 lanes_per_walker=lanes)
+                 lanes_per_walker=lanes, precision=prec)
     for n in (1, 2, 3, 999, 4000, 7):   # odd counts: the Philox pair straddles calls
         o.sweep(n)
         g.sweep(n)
         _compare(o, g)
 
 
-@pytest.mark.parametrize("sampler", SAMPLERS)
-def test_cycles_bit_exact_L8_3x3(P, sampler):
+@pytest.mark.parametrize("sampler,prec", [(0, 0), (0, 1), (1, 0)])
+def test_cycles_bit_exact_L8_3x3(P, sampler, prec):
     """The 2D REWL workload at L = 8 (3 x 3 windows at 75% overlap, 4 walkers
     per window, exchange every 10^4 trials): whole cycles of sampling,
     exchange (Eq. 2) and flatness checks stay bit-identical, through several
     iteration advances."""
     o, g = _pair(P, L=8, n_win_E=3, n_win_M=3, walkers_per_window=4, exchange_interval=10000,
-                 seed=20152811, sampler=sampler)
+                 seed=20152811, sampler=sampler, precision=prec)
     for chunk in (1, 3, 40, 100, 150):
         o.run_cycles(chunk)
         g.run_cycles(chunk)
@@ -126,23 +127,25 @@ def test_cycles_bit_exact_L8_3x3(P, sampler):
     assert o.info()["exch_accept"] > 0
 
 
-@pytest.mark.parametrize("sampler,wpb,lanes", [(0, 3, 32), (0, 8, 32), (0, 3, 8), (0, 2, 16), (1, 8, 0)])
-def test_cycles_with_check_interval_and_walkers_per_block(P, sampler, wpb, lanes):
+@pytest.mark.parametrize("sampler,wpb,lanes,prec", [(0, 3, 32, 0), (0, 8, 32, 1), (0, 3, 8, 1), (0, 2, 16, 0),
+                                                     (1, 8, 0, 0)])
+def test_cycles_with_check_interval_and_walkers_per_block(P, sampler, wpb, lanes, prec):
     """check_every > 1 (graph of several cycles) and a block size that leaves
     a ragged last block."""
     o, g = _pair(P, L=6, n_win_E=3, n_win_M=2, walkers_per_window=5, exchange_interval=3001,
-                 check_every=3, walkers_per_block=wpb, seed=5, sampler=sampler, lanes_per_walker=lanes)
+                 check_every=3, walkers_per_block=wpb, seed=5, sampler=sampler, lanes_per_walker=lanes,
+                 precision=prec)
     for chunk in (2, 7, 60):
         o.run_cycles(chunk)
         g.run_cycles(chunk)
         _compare(o, g)
 
 
-@pytest.mark.parametrize("sampler", SAMPLERS)
-def test_run_to_done_L4_and_join(P, sampler):
+@pytest.mark.parametrize("sampler,prec", [(0, 0), (0, 1), (1, 0)])
+def test_run_to_done_L4_and_join(P, sampler, prec):
     """Serial WL at L = 4 run to ln f <= 1e-6: identical trajectory to the end,
     done flag, and the joined table equal to the oracle's within 1e-9."""
-    o, g = _pair(P, L=4, exchange_interval=10000, seed=20151811, sampler=sampler)
+    o, g = _pair(P, L=4, exchange_interval=10000, seed=20151811, sampler=sampler, precision=prec)
     while not o.info()["done"]:
         o.run_cycles(64)
     st = g.run_cycles(o.info()["cycle"] + 5)   # extra cycles after done do nothing
@@ -222,7 +225,7 @@ def test_full_size_L32_batched_cycles(P):
     from paper_1508_02748_gb300.workloads import REWL_L32 as w
     o, g = _pair(P, L=w.L, n_win_E=w.n_win_E, n_win_M=w.n_win_M, walkers_per_window=w.walkers_per_window,
                  exchange_interval=w.exchange_interval, check_every=w.check_every, seed=w.seed(0),
-                 drive_budget=10**8)
+                 drive_budget=10**8, precision=1)
     o.run_cycles(2)
     g.run_cycles(2)
     so, spo = o.walkers()
