@@ -61,6 +61,12 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "f32x2"],
+                    help="ln g tables (default: the workload's: fp64)")
+    ap.add_argument("--sampler", default="warp", choices=["warp", "thread"])
+    ap.add_argument("--time-to", action="store_true",
+                    help="run the workload to its final ln f and report the wall time and ln g error")
     return ap.parse_args()
 
 
@@ -189,12 +195,21 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def _config_dict(w, l2: str) -> dict:
+def _config_dict(w, l2: str, precision: str = "fp64", sampler: str = "oracle") -> dict:
     return {"workload": w.name, "L": w.L, "windows": f"{w.n_win_E}x{w.n_win_M}",
             "overlap": w.overlap_E, "walkers_per_window": w.walkers_per_window,
             "walkers": w.n_walkers, "exchange_interval": w.exchange_interval,
-            "check_every": w.check_every, "ln_g": "fp64", "step": "one cycle: sample + exchange + check",
-            "l2": l2}
+            "check_every": w.check_every, "ln_g": precision, "sampler": sampler,
+            "step": "one cycle: sample + exchange + check", "l2": l2}
+
+
+def exact_lngE(L: int):
+    """Exact ln g(E) stored under tests/golden (written from the closed form)."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"lngE_L{L}.txt")
+    if not os.path.exists(path):
+        return None
+    return np.loadtxt(path)
 
 
 # ------------------------------------------------------------------- GPU ----
@@ -219,7 +234,11 @@ def run_gpu(args, w):
             import torch.distributed as dist
             dist.barrier()
 
-    cfg = P.Config.from_workload(w, replicate=rank, drive_budget=10**8)
+    prec = {"fp64": P.FP64, "f32x2": P.F32X2}[args.precision]
+    smp = {"warp": P.SAMPLER_WARP, "thread": P.SAMPLER_THREAD}[args.sampler]
+    cfg = P.Config.from_workload(w, replicate=rank, drive_budget=10**8, precision=prec, sampler=smp)
+    if args.time_to:
+        return run_time_to(args, w, cfg, dev)
     run = P.REWL(cfg, device=str(dev))
     s = run.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -271,7 +290,8 @@ def run_gpu(args, w):
     achieved = OPS_PER_TRIAL * trials_per_step / sweep_s
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": achieved / peak_ops, "traffic": None,
-            "kernel": "k_sweep_fp64", "kernel_ms_mean": sweep_s * 1e3,
+            "kernel": "k_sweep_tree" if args.sampler == "warp" else "k_sweep_fp64",
+            "kernel_ms_mean": sweep_s * 1e3,
             "kernel_share_of_step": sum(sweep_ms) / total_ms,
             "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x median SM clock {mhz:.0f} MHz (derived)"}
 
@@ -300,11 +320,13 @@ def run_gpu(args, w):
         run2.close()
 
     if rank == 0:
-        cpu = oracle_rate(w, args.cpu_seconds)
+        cpu = None if args.no_cpu else oracle_rate(w, args.cpu_seconds)
         line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": _config_dict(w, "flushed between steps (256 MiB write, outside the step events)"),
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2"}[args.precision],
+                "data": "synthetic",
+                "config": _config_dict(w, "flushed between steps (256 MiB write, outside the step events)",
+                                       args.precision, args.sampler),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
                 "clocks": clk,
                 "run": {"iteration": st["iteration"], "lnf": st["lnf"], "exch_accepts": st["exch_accepts"],
@@ -316,11 +338,44 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+def run_time_to(args, w, cfg, dev):
+    """Wall time from the first cycle until the iteration with ln f <= lnf_final
+    is flat, and the error of the joined E marginal against the exact g(E)."""
+    import numpy as np
+    import torch
+
+    import paper_1508_02748_gb300 as P
+    run = P.REWL(cfg, device=str(dev))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = run.status()
+    chunk = 64 * w.check_every
+    while not st["done"]:
+        st = run.run_cycles(chunk)
+    elapsed = time.perf_counter() - t0
+    mE = run.lng(P.LNG_MARGINAL_E)
+    ex = exact_lngE(w.L)
+    eps = None
+    if ex is not None:
+        ok = np.isfinite(ex) & (ex > 0) & np.isfinite(mE)
+        eps = float(np.mean(np.abs(mE[ok] - ex[ok]) / ex[ok]))
+    line = {"metric": "time-to-ln f<=%g" % w.lnf_final, "value": elapsed, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": {"fp64": "f64", "f32x2": "f32x2"}[args.precision],
+            "data": "synthetic", "config": _config_dict(w, "n/a", args.precision, args.sampler),
+            "iterations": st["iteration"], "cycles": st["cycles"], "trials_per_walker": st["trials"],
+            "lnf_final": st["lnf"], "mean_eps_E_marginal_vs_exact": eps,
+            "exchange_acceptance": st["exch_accepts"] / max(1, st["exch_attempts"])}
+    print(json.dumps(line), flush=True)
+    run.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3:
         args.warmup = 3
     w = workloads.ALL[args.workload]
+    if args.precision is None:
+        args.precision = "fp64"
     if args.impl == "reference":
         run_reference(args, w)
     else:
