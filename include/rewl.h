@@ -185,6 +185,31 @@ const char *rewl_last_error(const rewl_t *h);
 /* Releases the handle (not the workspace). */
 int rewl_destroy(rewl_t *h);
 
+/* Joined ln g(E,M) of tables already on the device, with no memory
+ * allocated by the call.  The paper has no counterpart: this serves callers
+ * that cannot allocate device memory (inside a region being captured into a
+ * CUDA graph, under an external allocator that owns all device memory, or
+ * with a fixed memory budget) but own their inputs and output.
+ *   cfg: the configuration the tables were sampled with (geometry, walkers).
+ *   d_lng, d_H: device pointers, n_walkers x window_bins entries each,
+ *     walker-major, [e][m] within a walker (the layout rewl_get_tables
+ *     returns): ln g as double, H as int32 (-1 = never visited).
+ *   d_out: device pointer to (N+1) x (N+1) doubles, [e][m]: the merged,
+ *     joined (Eqs. 3-4) and normalised (sum g = 2^N) table, -inf where no
+ *     walker visited; the same result as rewl_get_lng(REWL_LNG_JOINED).
+ *   stream: cudaStream_t (NULL = default); returns after the work is done.
+ * Working memory comes from one fixed 8 MiB __device__ array in the library
+ * (held on every GPU that loads it until the process exits); a geometry whose
+ * join needs more gets REWL_E_CAPACITY (roughly L <= 16 fits).  The first call
+ * on a device looks the array up (cudaGetSymbolAddress) with that device
+ * current: make it before any stream capture.  All calls share the array and
+ * it keeps the last call's contents; calls that overlap on the GPU race and
+ * must be serialised by the caller.  Errors: REWL_E_INVALID, REWL_E_CAPACITY,
+ * REWL_E_JOIN, REWL_E_CUDA; rewl_noalloc_last_error() gives the message. */
+int rewl_join_noalloc(const rewl_config *cfg, const double *d_lng, const int32_t *d_H, double *d_out,
+                      void *stream);
+const char *rewl_noalloc_last_error(void);
+
 /* Device Philox4x32-10 (the generator every random draw of the library uses;
  * Salmon et al., SC'11): d_out[4i..4i+3] = Philox(d_ctr[4i..4i+3], key).
  * d_ctr, d_out: device pointers to 4n uint32; key: host pointer to 2 uint32. */

@@ -54,6 +54,10 @@ int fail(rewl_t *h, int code, const char *fmt, ...)
             return fail((h), REWL_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+}  // namespace
+
+namespace rewl {
+
 // ----------------------------------------------------------- geometry ----
 
 // Equal-sized overlapping windows over `bins` bins (Sec. 2, Fig. 1b; Sec. 3
@@ -106,11 +110,6 @@ struct Layout {
     size_t fail, total;
 };
 
-struct Dims {
-    int L, N, wpr, nwords, nE, nM, W, nwin, nwalk, wE, wM, T;
-    long long tstride;
-};
-
 int check_config(const rewl_config *c, const char **why)
 {
     if (!c) { *why = "null config"; return REWL_E_INVALID; }
@@ -150,6 +149,10 @@ Dims dims_of(const rewl_config *c)
     d.tstride = ((long long)d.T + 63) / 64 * 64;
     return d;
 }
+
+}  // namespace rewl
+
+namespace {
 
 Layout layout_of(const Dims &d)
 {

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -127,5 +128,15 @@ cudaError_t launch_join(const Params &p, const JoinScratch &j, cudaStream_t s);
 cudaError_t launch_marginal_e(const Params &p, const JoinScratch &j, cudaStream_t s);
 
 enum : int { DECIDE_XSTEP = 1, DECIDE_CYCLE = 2, DECIDE_CHECK = 4 };
+
+// Host-side geometry and configuration helpers (rewl_api.cu).
+struct Dims {
+    int L, N, wpr, nwords, nE, nM, W, nwin, nwalk, wE, wM, T;
+    long long tstride;
+};
+void axis_windows(int bins, int n, double overlap, std::vector<int> &lo, std::vector<int> &hi);
+bool bin_can_hold(int L, int e, int m);
+int check_config(const rewl_config *c, const char **why);
+Dims dims_of(const rewl_config *c);
 
 }  // namespace rewl

@@ -73,6 +73,8 @@ SIGNATURES = {
     "rewl_last_error": (ctypes.c_char_p, [_P]),
     "rewl_destroy": (ctypes.c_int, [_P]),
     "rewl_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P]),
+    "rewl_join_noalloc": (ctypes.c_int, [ctypes.POINTER(rewl_config), _P, _P, _P, _P]),
+    "rewl_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
