@@ -69,6 +69,16 @@ struct RingEntry {
     float lnu;     // ln u in float
 };
 
+// Per-walker exchange area of one step (shared memory): the lanes of a
+// group trade their trial results through it instead of warp shuffles.
+struct Mailbox {
+    int move[32];                  // packed (de, dm) of each lane's own trial
+    int after[8];                  // bin after trial t+k on the true path
+    int leafpos;                   // the leaf's new (e, m)
+    int pad;
+    unsigned long long flips;      // register lattice: the path's flip mask
+};
+
 template <int G>
 struct TreeShape {
     static constexpr int DEPTH = G == 32 ? 4 : G == 16 ? 3 : G == 8 ? 2 : 1;
@@ -138,7 +148,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
 
     unsigned char *base = smem_raw + (size_t)slot * smem_per_walker;
     RingEntry *ring = reinterpret_cast<RingEntry *>(base);
-    uint32_t *lat = reinterpret_cast<uint32_t *>(base + RING * sizeof(RingEntry));
+    Mailbox *box = reinterpret_cast<Mailbox *>(base + RING * sizeof(RingEntry));
+    uint32_t *lat = reinterpret_cast<uint32_t *>(base + RING * sizeof(RingEntry) + sizeof(Mailbox));
     const int L = p.L, nwords = L * WPR;
     const int T = p.T;
     Elem *g_tab = (PREC == REWL_FP64) ? reinterpret_cast<Elem *>(p.lng) : reinterpret_cast<Elem *>(p.lng2);
@@ -147,7 +158,7 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     Elem *tl;
     int32_t *tH;
     if (SMT) {
-        tl = reinterpret_cast<Elem *>(base + RING * sizeof(RingEntry) + ((nwords * 4 + 15) & ~15));
+        tl = reinterpret_cast<Elem *>(base + RING * sizeof(RingEntry) + sizeof(Mailbox) + ((nwords * 4 + 15) & ~15));
         tH = reinterpret_cast<int32_t *>(tl + T);
         for (int k = gl; k < T; k += G) { tl[k] = g_tab[k]; tH[k] = gH[k]; }
     } else {
@@ -284,11 +295,13 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         // ---- 2. the history's earlier trials: moves from the lanes that took them
         // (a history that accepts a move out of the window is never the true
         // path; its bins are clamped below only to keep its reads in bounds)
+        box->move[gl] = pack;
+        __syncwarp(gmask);
         int ce = e, cm = m, cbin = ci;
         int vb[DEPTH];               // bin after each earlier trial (-1 past the own depth)
         #pragma unroll
         for (int k = 0; k < DEPTH; ++k) {
-            const int pk = __shfl_sync(gmask, pack, srck[k], G);
+            const int pk = box->move[srck[k]];
             if (k < dl && ((hist >> k) & 1)) {
                 const int de = (pk & 7) - 2, dm = ((pk >> 3) & 3) - 1;
                 ce += de;
@@ -328,46 +341,64 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         acc = live ? acc : 0;
         const int after = acc ? nbin : cbin;   // bin after the own trial, under the own history
 
-        // ---- follow the true path from the root
+        // ---- the true path, walked from the root over the ballot (children of
+        // lane l at depth k are l + 2^k (reject) and l + 2^(k+1) (accept))
         const unsigned bal = (__ballot_sync(gmask, acc) >> (grp * G)) & GBITS;
-        int path = 0, node = 0, leaf = 0;
+        int path = 0, node = 0;
         #pragma unroll
         for (int k = 0; k <= DEPTH; ++k) {
             if (k <= D) {
-                leaf = node;
-                const int b = (bal >> node) & 1u;
-                path |= b << k;
-                node += (1 + b) << k;
+                const int bk = (int)((bal >> node) & 1u);
+                path |= bk << k;
+                node += (1 + bk) << k;
             }
         }
+        const bool onp = dl <= D && hist == (path & ((1 << dl) - 1));
+        const bool is_leaf = onp && dl == D;
 
-        // ---- commit: lane k takes trial t+k of the path
-        const int pk_src = (1 << (gl & 31)) - 1 + (path & ((1 << (gl & 31)) - 1));
-        const int xs = __shfl_sync(gmask, after, gl <= D ? pk_src : 0, G);
-        const int X = gl <= D ? xs : -1 - gl;   // bin after trial t+gl (unique dummies past D)
-        const unsigned mm = (__match_any_sync(gmask, X) >> (grp * G)) & GBITS;
-        const int C = __shfl_sync(gmask, X, D, G);
-        const int cC = __popc(__shfl_sync(gmask, mm, D, G));
-        const bool b0_seen = ((__ballot_sync(gmask, X == ci) >> (grp * G)) & ((2u << D) - 1u)) != 0;
+        // ---- commit: the on-path lane of depth k takes trial t+k
+        if (onp) box->after[dl] = after;
+        if (is_leaf) {
+            box->leafpos = ((acc ? en_o : ce) << 13) | (acc ? mn_o : cm);
+            if (REG) box->flips = fm ^ (acc ? (1ull << (me.a & 63u)) : 0ull);
+        }
+        __syncwarp(gmask);
+        int av[DEPTH + 1];
+        #pragma unroll
+        for (int k = 0; k <= DEPTH; ++k) av[k] = k <= D ? box->after[k] : -1;
+        const int lp = box->leafpos;
+        const int ne = lp >> 13, nm = lp & 0x1FFF;
+        const int C = (ne - R.x) * wM + (nm - R.z);
+        int cC = 0;
+        bool b0_seen = false;
+        #pragma unroll
+        for (int k = 0; k <= DEPTH; ++k) {
+            cC += (av[k] == C);
+            b0_seen |= (av[k] == ci);
+        }
         if (REG) {
-            // the path's flips: the leaf's history plus the leaf's own trial if accepted
-            const unsigned long long fl = fm ^ (acc ? (1ull << (me.a & 63u)) : 0ull);
-            lat64 ^= __shfl_sync(gmask, fl, leaf, G);
-        } else if (gl <= D && ((path >> gl) & 1)) {
-            uint32_t fs = sa[0];
-            #pragma unroll
-            for (int k = 1; k <= DEPTH; ++k) if (gl == k) fs = sa[k];
-            const int fi = fs & 255, fj = (fs >> 8) & 255;
+            lat64 ^= box->flips;
+        } else if (onp && acc) {
+            const int fi = me.a & 255, fj = (me.a >> 8) & 255;
             atomicXor(&lat[fi * WPR + ((WPR == 1) ? 0 : (fj >> 5))], 1u << (fj & 31));
         }
-        // write-back of a bin the walker leaves in this step (all its visits)
+        // first visit of this lane's bin among the path's trials, and its count
+        bool firstv = true;
+        int cntv = 0;
+        #pragma unroll
+        for (int k = 0; k <= DEPTH; ++k) {
+            if (k < dl && av[k] == after) firstv = false;
+            cntv += (av[k] == after);
+        }
+        // write-back of a bin the walker leaves in this step (all its visits),
+        // by the shallowest on-path lane that ended in it
         {
-            const bool own = gl <= D && (__ffs(mm) - 1) == gl && X != C;
+            const bool own = onp && firstv && after != C;
             const bool entry_left = gl == G - 1 && C != ci && !b0_seen && hq > 0;
             if (own || entry_left) {
-                const int Xw = own ? X : ci;
+                const int Xw = own ? after : ci;
                 const bool isci = Xw == ci;
-                const int cnt = own ? __popc(mm) : 0;
+                const int cnt = own ? cntv : 0;
                 const Val v0 = isci ? lbase : TB::load(tl, Xw);
                 const int h0 = isci ? hbase : tH[Xw];
                 const int nv = cnt + (isci ? lq : 0), nh = cnt + (isci ? hq : 0);
@@ -378,12 +409,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             }
         }
         // the group adopts the state after the last trial
-        {
-            const int em_leaf = acc ? ((en_o << 16) | mn_o) : ((ce << 16) | cm);
-            const int em = __shfl_sync(gmask, em_leaf, leaf, G);
-            e = em >> 16;
-            m = em & 0xFFFF;
-        }
+        e = ne;
+        m = nm;
         if (C == ci) {
             lq += cC;
             hq += cC;
@@ -424,11 +451,11 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     if (gl == 0 && err) atomicOr(&p.st->error, ERR_OVERFLOW);
 }
 
-// Shared memory per walker: ring, lattice (16-byte padded) and, when staged,
+// Shared memory per walker: ring, mailbox, lattice (16-byte padded) and, when staged,
 // the tables (8-byte ln g entries in either format, 4-byte H).
 size_t tree_smem_per_warp(const Params &p, bool smt)
 {
-    size_t b = RING * sizeof(RingEntry) + (((size_t)p.nwords * 4 + 15) & ~(size_t)15);
+    size_t b = RING * sizeof(RingEntry) + sizeof(Mailbox) + (((size_t)p.nwords * 4 + 15) & ~(size_t)15);
     if (smt) b += (size_t)p.T * (8 + sizeof(int32_t));
     return (b + 15) & ~(size_t)15;
 }
