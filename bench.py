@@ -70,6 +70,29 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_max_ms(local_ms: float, world: int, device) -> float:
+    """Max over ranks of a per-rank time (the contract's max-over-ranks clock)."""
+    if world <= 1:
+        return local_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(trials_per_step: int, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job trials/s: every rank runs an independent replica of the
+    workload (same size, its own seed), so the job does world x the trials
+    in the slowest rank's time."""
+    return trials_per_step * steps * world / (total_ms / 1e3)
+
+
+def replica_seed_index(rank: int) -> int:
+    """Replicate index of a rank's run (its seed is 20150811 + 1000 id + this)."""
+    return rank
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -236,7 +259,8 @@ def run_gpu(args, w):
 
     prec = {"fp64": P.FP64, "f32x2": P.F32X2}[args.precision]
     smp = {"warp": P.SAMPLER_WARP, "thread": P.SAMPLER_THREAD}[args.sampler]
-    cfg = P.Config.from_workload(w, replicate=rank, drive_budget=10**8, precision=prec, sampler=smp)
+    cfg = P.Config.from_workload(w, replicate=replica_seed_index(rank), drive_budget=10**8, precision=prec,
+                                 sampler=smp)
     if args.time_to:
         return run_time_to(args, w, cfg, dev)
     run = P.REWL(cfg, device=str(dev))
@@ -273,14 +297,9 @@ def run_gpu(args, w):
     clk = clocks.stop()
     step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
     sweep_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(sum(step_ms), world, dev)
     st = run.status()
-    value = trials_per_step * K * world / (total_ms / 1e3)
+    value = aggregate_rate(trials_per_step, K, world, total_ms)
 
     # roofline of the sampling kernel: ALU operations of the method per launch
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
