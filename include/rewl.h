@@ -55,6 +55,8 @@ extern "C" {
 /* ln g arithmetic of the sampling tables. */
 #define REWL_FP64 0             /* double per bin */
 #define REWL_F32X2 1            /* compensated pair of floats (hi, lo) per bin */
+#define REWL_F32 2              /* one float per bin, plain accumulation: increments below half an
+                                   ulp of ln g are lost (precision-study demonstration; warp sampler) */
 
 /* Sampling kernels (same trajectory, different mapping onto the GPU). */
 #define REWL_SAMPLER_WARP 0     /* 8/16/32 lanes per walker, 3/4/5 trials resolved per step */
@@ -75,7 +77,7 @@ typedef struct rewl_config {
     double overlap_E;           /* overlap fraction of adjacent windows, [0, 1) */
     double overlap_M;
     int32_t walkers_per_window; /* independent walkers per window (Sec. 2), >= 1 */
-    int32_t precision;          /* REWL_FP64 or REWL_F32X2 */
+    int32_t precision;          /* REWL_FP64, REWL_F32X2 or REWL_F32 */
     double lnf_init;            /* ln f of the first iteration (> 0) */
     double lnf_final;           /* run ends after the first flat iteration with ln f <= this */
     double lnf_factor;          /* ln f <- ln f * factor; 0.5 is f -> sqrt(f) (Sec. 2) */

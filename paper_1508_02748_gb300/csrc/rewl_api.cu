@@ -119,7 +119,7 @@ int check_config(const rewl_config *c, const char **why)
     if (c->n_win_E < 1 || c->n_win_M < 1 || c->n_win_E > N + 1 || c->n_win_M > N + 1) { *why = "bad window grid"; return REWL_E_INVALID; }
     if (!(c->overlap_E >= 0.0 && c->overlap_E < 1.0 && c->overlap_M >= 0.0 && c->overlap_M < 1.0)) { *why = "overlap must be in [0, 1)"; return REWL_E_INVALID; }
     if (c->walkers_per_window < 1 || c->walkers_per_window > 1024) { *why = "walkers_per_window must be in [1, 1024]"; return REWL_E_INVALID; }
-    if (c->precision != REWL_FP64 && c->precision != REWL_F32X2) { *why = "unknown precision"; return REWL_E_INVALID; }
+    if (c->precision != REWL_FP64 && c->precision != REWL_F32X2 && c->precision != REWL_F32) { *why = "unknown precision"; return REWL_E_INVALID; }
     if (!(c->lnf_init > 0.0 && c->lnf_final > 0.0 && c->lnf_factor > 0.0 && c->lnf_factor < 1.0)) { *why = "bad ln f schedule"; return REWL_E_INVALID; }
     if (!(c->flatness > 0.0 && c->flatness <= 1.0)) { *why = "flatness must be in (0, 1]"; return REWL_E_INVALID; }
     if (c->exchange_interval < 1) { *why = "exchange_interval must be >= 1"; return REWL_E_INVALID; }
@@ -353,6 +353,7 @@ extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spin
     p.wflat = (int32_t *)(base + lay.wflat);
     p.lng = (double *)(base + lay.lng);
     p.lng2 = (float2 *)(base + lay.lng);
+    p.lng1 = (float *)(base + lay.lng);
     p.H = (int32_t *)(base + lay.H);
     p.st = (DevState *)(base + lay.st);
     JoinScratch &j = h->j;
@@ -594,12 +595,18 @@ extern "C" int rewl_get_tables(rewl_t *h, double *host_lng, int32_t *host_H, siz
         if (p.precision == REWL_FP64) {
             CK(h, cudaMemcpy2DAsync(host_lng, 8 * (size_t)p.T, p.lng, 8 * (size_t)p.tstride, 8 * (size_t)p.T,
                                     p.nwalk, cudaMemcpyDeviceToHost, h->stream));
-        } else {
+        } else if (p.precision == REWL_F32X2) {
             std::vector<float2> tmp(n);
             CK(h, cudaMemcpy2DAsync(tmp.data(), 8 * (size_t)p.T, p.lng2, 8 * (size_t)p.tstride, 8 * (size_t)p.T,
                                     p.nwalk, cudaMemcpyDeviceToHost, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
             for (size_t i = 0; i < n; ++i) host_lng[i] = (double)tmp[i].x + (double)tmp[i].y;
+        } else {
+            std::vector<float> tmp(n);
+            CK(h, cudaMemcpy2DAsync(tmp.data(), 4 * (size_t)p.T, p.lng1, 4 * (size_t)p.tstride, 4 * (size_t)p.T,
+                                    p.nwalk, cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            for (size_t i = 0; i < n; ++i) host_lng[i] = (double)tmp[i];
         }
     }
     if (host_H)
@@ -618,13 +625,19 @@ extern "C" int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t 
         if (p.precision == REWL_FP64) {
             CK(h, cudaMemcpy2DAsync(p.lng, 8 * (size_t)p.tstride, host_lng, 8 * (size_t)p.T, 8 * (size_t)p.T,
                                     p.nwalk, cudaMemcpyHostToDevice, h->stream));
-        } else {
+        } else if (p.precision == REWL_F32X2) {
             std::vector<float2> tmp(n);
             for (size_t i = 0; i < n; ++i) {
                 const float hi = (float)host_lng[i];
                 tmp[i] = make_float2(hi, (float)(host_lng[i] - (double)hi));
             }
             CK(h, cudaMemcpy2DAsync(p.lng2, 8 * (size_t)p.tstride, tmp.data(), 8 * (size_t)p.T, 8 * (size_t)p.T,
+                                    p.nwalk, cudaMemcpyHostToDevice, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        } else {
+            std::vector<float> tmp(n);
+            for (size_t i = 0; i < n; ++i) tmp[i] = (float)host_lng[i];
+            CK(h, cudaMemcpy2DAsync(p.lng1, 4 * (size_t)p.tstride, tmp.data(), 4 * (size_t)p.T, 4 * (size_t)p.T,
                                     p.nwalk, cudaMemcpyHostToDevice, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
         }

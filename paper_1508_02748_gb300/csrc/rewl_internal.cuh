@@ -87,6 +87,7 @@ struct Params {
     int32_t *wflat;   // last flatness verdict
     double *lng;      // REWL_FP64: nwalk x tstride
     float2 *lng2;     // REWL_F32X2: nwalk x tstride (hi, lo)
+    float *lng1;      // REWL_F32: nwalk x tstride
     int32_t *H;       // nwalk x tstride, -1 = never visited
     DevState *st;
 };

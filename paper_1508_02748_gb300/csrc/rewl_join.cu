@@ -26,6 +26,7 @@ namespace {
 __device__ __forceinline__ double lng_at(const Params &p, size_t i)
 {
     if (p.precision == REWL_FP64) return p.lng[i];
+    if (p.precision == REWL_F32) return (double)p.lng1[i];
     const float2 v = p.lng2[i];
     return (double)v.x + (double)v.y;
 }

@@ -34,6 +34,7 @@ __device__ __forceinline__ uint32_t sbit(const uint32_t *sm, int nb, int r, int 
 __device__ __forceinline__ double lng_read(const Params &p, size_t i)
 {
     if (p.precision == REWL_FP64) return p.lng[i];
+    if (p.precision == REWL_F32) return (double)p.lng1[i];
     const float2 v = p.lng2[i];
     return (double)v.x + (double)v.y;
 }
@@ -541,6 +542,8 @@ __global__ void k_tables_from_double(Params p, const double *in)
         const double v = in[i];
         if (p.precision == REWL_FP64) {
             p.lng[w * p.tstride + b] = v;
+        } else if (p.precision == REWL_F32) {
+            p.lng1[w * p.tstride + b] = (float)v;
         } else {
             const float hi = (float)v;
             p.lng2[w * p.tstride + b] = make_float2(hi, (float)(v - (double)hi));

@@ -123,6 +123,22 @@ struct Tab<REWL_F32X2> {
     __device__ static Val add(Val v, int n, double, float lnf32) { return add2(v, __fmul_rn((float)n, lnf32)); }
 };
 
+// Plain float (demonstration of the precision loss the compensated pair
+// avoids): each visit adds ln f to a single float and rounds.
+template <>
+struct Tab<REWL_F32> {
+    using Elem = float;
+    using Val = float;
+    __device__ static Val load(const Elem *t, int i) { return t[i]; }
+    __device__ static float approx(Val v) { return v; }
+    __device__ static double exact(Val v) { return (double)v; }
+    __device__ static Val add(Val v, int n, double, float lnf32)
+    {
+        for (int i = 0; i < n; ++i) v = __fadd_rn(v, lnf32);
+        return v;
+    }
+};
+
 }  // namespace
 
 // REG: the lattice (N <= 64 sites, bit i*L + j) is held in a 64-bit register
@@ -152,7 +168,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     uint32_t *lat = reinterpret_cast<uint32_t *>(base + RING * sizeof(RingEntry) + sizeof(Mailbox));
     const int L = p.L, nwords = L * WPR;
     const int T = p.T;
-    Elem *g_tab = (PREC == REWL_FP64) ? reinterpret_cast<Elem *>(p.lng) : reinterpret_cast<Elem *>(p.lng2);
+    Elem *g_tab = (PREC == REWL_FP64) ? reinterpret_cast<Elem *>(p.lng)
+                : (PREC == REWL_F32X2) ? reinterpret_cast<Elem *>(p.lng2) : reinterpret_cast<Elem *>(p.lng1);
     g_tab += (size_t)w * p.tstride;
     int32_t *gH = p.H + (size_t)w * p.tstride;
     Elem *tl;
@@ -334,7 +351,10 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         const float d32 = c32 - n32;
         const float M = (fabsf(c32) + fabsf(n32) + fabsf(cb32) + fabsf(nb32) + fabsf(me.lnu)) * 0x1p-20f + 0x1p-20f;
         int acc = (me.lnu < d32 - M) ? 1 : 0;
-        if (live && !acc && !(me.lnu > d32 + M)) {
+        if constexpr (PREC == REWL_F32) {
+            // plain float: the values the walker sees are the rounded sums
+            acc = (me.lnu < TB::add(cbase, ccnt, lnf, lnf32) - TB::add(nbase, ncnt, lnf, lnf32)) ? 1 : 0;
+        } else if (live && !acc && !(me.lnu > d32 + M)) {
             const double delta = fma((double)ccnt, lnf, TB::exact(cbase)) - fma((double)ncnt, lnf, TB::exact(nbase));
             acc = (delta >= 0.0 || log(unit_open_d(me.xu)) < delta) ? 1 : 0;
         }
@@ -491,7 +511,8 @@ cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int 
     return go(k_sweep_tree<W_, S_, 8, P_, false>);
 #define REWL_TREE_P(W_, S_)                                                \
     if (p.precision == REWL_FP64) { REWL_TREE_G(W_, S_, REWL_FP64) }       \
-    else { REWL_TREE_G(W_, S_, REWL_F32X2) }
+    else if (p.precision == REWL_F32X2) { REWL_TREE_G(W_, S_, REWL_F32X2) } \
+    else { REWL_TREE_G(W_, S_, REWL_F32) }
     if (p.wpr == 1) {
         if (smt) { REWL_TREE_P(1, true) } else { REWL_TREE_P(1, false) }
     } else {

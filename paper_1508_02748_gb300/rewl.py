@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "librewl.so")
 REWL_OK = 0
 ERRORS = {-1: "INVALID", -2: "CUDA", -3: "TIMEOUT", -4: "UNREACHABLE", -5: "OVERFLOW",
           -6: "BUDGET", -7: "JOIN", -8: "CAPACITY"}
-FP64, F32X2 = 0, 1
+FP64, F32X2, F32 = 0, 1, 2
 PART_SAMPLE, PART_REST = 1, 2
 SAMPLER_WARP, SAMPLER_THREAD = 0, 1
 LNG_JOINED, LNG_MARGINAL_E = 0, 1

@@ -237,3 +237,26 @@ def test_full_size_L32_batched_cycles(P):
     np.testing.assert_array_equal(Hg, Ho)
     np.testing.assert_array_equal(lg, lo)
     assert g.status()["exch_attempts"] == o.info()["exch_attempt"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_empty_windows_cycles_and_join(P, prec):
+    """L = 8, 6 x 6 windows at 50% overlap: four windows hold no configuration
+    and get no walkers; sampling, exchange, checks and the join skip them
+    exactly as the oracle does."""
+    o, g = _pair(P, L=8, n_win_E=6, n_win_M=6, overlap_E=0.5, overlap_M=0.5, walkers_per_window=2,
+                 exchange_interval=4000, seed=31, drive_budget=10**8, precision=prec)
+    np.testing.assert_array_equal(g.windows(), o.windows())
+    assert (g.windows()[:, 4] == 0).sum() == 4
+    for chunk in (2, 30, 80):
+        o.run_cycles(chunk)
+        g.run_cycles(chunk)
+        _compare(o, g)
+    assert g.status()["n_walkers"] == 2 * 32
+    Jo, emo, mmo = o.join()
+    Jg, emg, mmg = g.lng(matches=True)
+    np.testing.assert_array_equal(emg, emo)
+    np.testing.assert_array_equal(mmg, mmo)
+    fin = np.isfinite(Jo)
+    assert np.array_equal(np.isfinite(Jg), fin)
+    np.testing.assert_allclose(Jg[fin], Jo[fin], rtol=1e-12, atol=1e-9)

@@ -271,3 +271,43 @@ def test_rewl_L8_short_run_tracks_exact():
     occ = np.isfinite(lgE) & (lgE > 0)
     eps = np.abs(mE[occ] - lgE[occ]) / lgE[occ]
     assert eps.mean() < 0.03
+
+
+def test_empty_windows_L8_6x6_geometry_and_join():
+    """Windows with no possible (E, M) bin (Sec. 1: cusps and empty regions)
+    are dropped; the join over the remaining windows still reconstructs the
+    exact table.  L = 8, 6 x 6 windows at 50% overlap: the four high-E windows
+    of the two extreme-M rows hold no configuration."""
+    gold = np.loadtxt(os.path.join(GOLD, "gEM_L8.txt"), dtype=np.float64)
+    lg = _lg(gold)
+    W = 2
+    r = OracleREWL(OracleConfig(L=8, n_win_E=6, n_win_M=6, overlap_E=0.5, overlap_M=0.5,
+                                walkers_per_window=W, seed=31, drive_budget=10**8))
+    w = r.windows()
+    inactive = sorted((k % 6, k // 6) for k in range(36) if not w[k, 4])
+    assert inactive == [(4, 0), (4, 5), (5, 0), (5, 5)]
+    for k in range(36):          # an empty window really holds no configuration
+        e0, e1, m0, m1, act = w[k]
+        assert bool(act) == bool((gold[e0:e1 + 1, m0:m1 + 1] > 0).any())
+    st, _ = r.walkers()
+    for k in range(st.shape[0]):
+        e0, e1, m0, m1, act = w[k // W]
+        if act:
+            assert e0 <= st[k, 0] <= e1 and m0 <= st[k, 1] <= m1
+    lng, H, toff = r.tables()
+    rng = np.random.default_rng(2)
+    for k in range(toff.size - 1):
+        e0, e1, m0, m1, act = w[k // W]
+        if not act:
+            continue
+        blk = lg[e0:e1 + 1, m0:m1 + 1]
+        seen = np.isfinite(blk)
+        lng[toff[k]:toff[k + 1]] = np.where(seen, blk + rng.normal() * 20, 0.0).ravel()
+        H[toff[k]:toff[k + 1]] = np.where(seen, 1, -1).ravel()
+    r.set_tables(lng, H)
+    J, em, mm = r.join()
+    occ = gold > 0
+    assert np.array_equal(np.isfinite(J), occ)
+    assert np.abs(J[occ] - lg[occ]).max() < 1e-8
+    r.run_cycles(3)               # sampling and exchange skip the empty windows
+    assert r.info()["exch_attempt"] >= 0
