@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default=workloads.REWL_L8.name, choices=sorted(workloads.ALL))
+    ap.add_argument("--workload", default=workloads.REWL_L8.name,
+                    choices=sorted(workloads.ALL) + [workloads.BATCH_NAME])
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -388,13 +389,99 @@ def run_time_to(args, w, cfg, dev):
     run.close()
 
 
+def run_gpu_batch(args):
+    """The uneven batch: 24 runs of L = 16, 24, 32, 48 advanced together by
+    one CUDA graph per step (K = 8 cycles of every run)."""
+    import numpy as np
+    import torch
+
+    import paper_1508_02748_gb300 as P
+    from paper_1508_02748_gb300 import build as pkg_build
+
+    rank, world, local = dist_env()
+    pkg_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    prec = {"fp64": P.FP64, "f32x2": P.F32X2}[args.precision]
+    wl = workloads.mixed_batch()
+    runs = [P.REWL(P.Config.from_workload(w, replicate=i + 24 * replica_seed_index(rank), drive_budget=10**8,
+                                          precision=prec), device=str(dev)) for i, w in enumerate(wl)]
+    batch = P.Batch(runs)
+    s = batch.stream
+    active = sum(r.status()["n_walkers"] for r in runs)
+    trials_per_step = batch.k * wl[0].exchange_interval * active
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            batch.enqueue()
+    s.synchronize()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(s)
+            batch.enqueue()
+            ev[k][1].record(s)
+    s.synchronize()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = reduce_max_ms(sum(ev[k][0].elapsed_time(ev[k][1]) for k in range(K)), world, dev)
+    value = aggregate_rate(trials_per_step, K, world, total_ms)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 1920.0
+    peak_ops = sm_count * ALU_LANES_PER_SM * mhz * 1e6
+    achieved = OPS_PER_TRIAL * trials_per_step / (total_ms / K / 1e3)
+    launches_per_step = sum(batch.k * 3 + 2 * (batch.k // r.cfg.check_every) for r in runs)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            cpu = oracle_rate(wl[0], args.cpu_seconds)
+            cpu["sample"] += " (the L=16 member of the batch, as the per-trial CPU cost)"
+        line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": workloads.BATCH_NAME, "runs": len(runs), "walkers": active,
+                           "L": [16, 24, 32, 48], "cycles_per_step": batch.k, "ln_g": args.precision,
+                           "sampler": "warp", "l2": "flushed between steps (256 MiB write, outside the step events)"},
+                "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                             "frac": achieved / peak_ops, "traffic": None, "kernel": "k_sweep_tree (24 concurrent)",
+                             "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x median SM clock {mhz:.0f} MHz "
+                                           "(derived); achieved over the whole step"},
+                "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches_per_step * K * world, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for r in runs:
+        r.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3:
         args.warmup = 3
-    w = workloads.ALL[args.workload]
-    if args.precision is None:
+    w = workloads.ALL.get(args.workload)
+    if args.precision is None and w is not None:
         args.precision = "fp64"
+    if args.workload == workloads.BATCH_NAME:
+        if args.precision is None or args.precision == "fp64":
+            args.precision = "f32x2" if args.precision is None else args.precision
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batch workload needs ~35 GB of oracle "
+                              "tables; time the oracle on a single run instead"}))
+            return
+        run_gpu_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -187,6 +187,28 @@ const char *rewl_last_error(const rewl_t *h);
 /* Releases the handle (not the workspace). */
 int rewl_destroy(rewl_t *h);
 
+/* A batch: several runs (any L, geometry or precision) advanced together.
+ * rewl_batch_create builds one CUDA graph whose parallel branches hold each
+ * run's cycle kernels on a stream of its own, so the runs sample concurrently
+ * on the GPU and one graph launch advances all of them by K cycles, K the
+ * least common multiple of their check_every (at most 64).  Each run keeps
+ * its own workspace and its trajectory is exactly the one it has when run
+ * alone.  The runs must each stand at a multiple of their own check_every
+ * cycles, must not be used on their own while the batch exists, and stay
+ * owned by the caller (rewl_batch_destroy does not destroy them).
+ *   runs: host array of n run handles (n >= 1); stream: the stream the
+ *   batch's graph is launched on (not NULL).
+ * rewl_batch_run_cycles runs n_cycles (a multiple of K) on every run and
+ * returns when they are done.  Errors: REWL_E_INVALID, REWL_E_CUDA. */
+typedef struct rewl_batch_s rewl_batch_t;
+int rewl_batch_create(rewl_t *const *runs, int n, void *stream, rewl_batch_t **out);
+int rewl_batch_cycles_per_launch(const rewl_batch_t *b, uint64_t *k);
+int rewl_batch_run_cycles(rewl_batch_t *b, uint64_t n_cycles);
+/* Queues one graph launch (K cycles of every run) on the batch stream and
+ * returns without waiting (for callers that time or overlap the stream). */
+int rewl_batch_enqueue(rewl_batch_t *b);
+int rewl_batch_destroy(rewl_batch_t *b);
+
 /* Joined ln g(E,M) of tables already on the device, with no memory
  * allocated by the call.  The paper has no counterpart: this serves callers
  * that cannot allocate device memory (inside a region being captured into a

@@ -7,4 +7,4 @@ argument-marshalling binding.  Nothing is loaded at import time; the first
 :class:`REWL` loads the library and fails loudly if it is missing.
 """
 from .rewl import (F32, F32X2, FP64, LNG_JOINED, LNG_MARGINAL_E, PART_REST, PART_SAMPLE, REWL,  # noqa: F401
-                   SAMPLER_THREAD, SAMPLER_WARP, Config, REWLError, load_library, philox)
+                   SAMPLER_THREAD, SAMPLER_WARP, Batch, Config, REWLError, load_library, philox)

@@ -700,3 +700,146 @@ extern "C" int rewl_philox(const uint32_t *d_ctr, const uint32_t *key, uint32_t 
     if (e != cudaSuccess) return fail(nullptr, REWL_E_CUDA, "philox: %s", cudaGetErrorString(e));
     return REWL_OK;
 }
+
+// ------------------------------------------------------------------ batch ----
+
+struct rewl_batch_s {
+    std::vector<rewl_t *> runs;
+    std::vector<cudaStream_t> streams;   // one per run, created by the batch
+    std::vector<cudaEvent_t> events;     // fork event + one join event per run
+    cudaStream_t stream;
+    cudaGraphExec_t graph;
+    unsigned long long k;                // cycles per graph launch
+    char err[512];
+};
+
+namespace {
+
+unsigned long long gcd_u(unsigned long long a, unsigned long long b)
+{
+    while (b) { const unsigned long long t = a % b; a = b; b = t; }
+    return a;
+}
+
+void batch_free(rewl_batch_t *b)
+{
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" int rewl_batch_create(rewl_t *const *runs, int n, void *stream, rewl_batch_t **out)
+{
+    if (!runs || n < 1 || !out || !stream) return fail(nullptr, REWL_E_INVALID, "batch: bad arguments");
+    rewl_batch_t *b = new (std::nothrow) rewl_batch_t();
+    if (!b) return fail(nullptr, REWL_E_INVALID, "out of host memory");
+    b->stream = (cudaStream_t)stream;
+    b->graph = nullptr;
+    b->k = 1;
+    for (int i = 0; i < n; ++i) {
+        rewl_t *h = runs[i];
+        if (!h) { batch_free(b); return fail(nullptr, REWL_E_INVALID, "batch: null run %d", i); }
+        const unsigned long long ce = (unsigned long long)h->cfg.check_every;
+        if (h->host_cycle % ce != 0) {
+            batch_free(b);
+            return fail(nullptr, REWL_E_INVALID, "batch: run %d is not at a multiple of its check_every", i);
+        }
+        b->k = b->k / gcd_u(b->k, ce) * ce;
+        if (b->k > 64) { batch_free(b); return fail(nullptr, REWL_E_INVALID, "batch: lcm of check_every above 64"); }
+        b->runs.push_back(h);
+    }
+    cudaError_t e;
+    b->events.resize(n + 1, nullptr);
+    b->streams.resize(n, nullptr);
+    for (int i = 0; i <= n; ++i)
+        if ((e = cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming)) != cudaSuccess) {
+            batch_free(b);
+            return fail(nullptr, REWL_E_CUDA, "batch: event: %s", cudaGetErrorString(e));
+        }
+    for (int i = 0; i < n; ++i)
+        if ((e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking)) != cudaSuccess) {
+            batch_free(b);
+            return fail(nullptr, REWL_E_CUDA, "batch: stream: %s", cudaGetErrorString(e));
+        }
+    // Capture: fork from the batch stream, K cycles of each run on its own
+    // stream, join back.  The runs' own streams are swapped for the capture.
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        batch_free(b);
+        return fail(nullptr, REWL_E_CUDA, "batch: begin capture: %s", cudaGetErrorString(e));
+    }
+    cudaError_t qe = cudaEventRecord(b->events[n], b->stream);
+    for (int i = 0; i < n && qe == cudaSuccess; ++i) {
+        rewl_t *h = b->runs[i];
+        cudaStream_t own = h->stream;
+        h->stream = b->streams[i];
+        qe = cudaStreamWaitEvent(h->stream, b->events[n], 0);
+        const unsigned long long ce = (unsigned long long)h->cfg.check_every;
+        for (unsigned long long c = 0; c < b->k && qe == cudaSuccess; ++c)
+            qe = queue_cycle(h, (c + 1) % ce == 0);
+        if (qe == cudaSuccess) qe = cudaEventRecord(b->events[i], h->stream);
+        if (qe == cudaSuccess) qe = cudaStreamWaitEvent(b->stream, b->events[i], 0);
+        h->stream = own;
+    }
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (qe != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        batch_free(b);
+        return fail(nullptr, REWL_E_CUDA, "batch: capture: %s",
+                    cudaGetErrorString(qe != cudaSuccess ? qe : e));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        batch_free(b);
+        return fail(nullptr, REWL_E_CUDA, "batch: instantiate: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return REWL_OK;
+}
+
+extern "C" int rewl_batch_cycles_per_launch(const rewl_batch_t *b, uint64_t *k)
+{
+    if (!b || !k) return REWL_E_INVALID;
+    *k = b->k;
+    return REWL_OK;
+}
+
+extern "C" int rewl_batch_run_cycles(rewl_batch_t *b, uint64_t n_cycles)
+{
+    if (!b) return REWL_E_INVALID;
+    if (n_cycles % b->k != 0) return REWL_E_INVALID;
+    for (uint64_t c = 0; c < n_cycles; c += b->k) {
+        const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) return fail(nullptr, REWL_E_CUDA, "batch launch: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return fail(nullptr, REWL_E_CUDA, "batch sync: %s", cudaGetErrorString(e));
+    for (rewl_t *h : b->runs) h->host_cycle += n_cycles;
+    for (rewl_t *h : b->runs) {
+        DevState ds;
+        const int rc = read_state(h, &ds);
+        if (rc) return rc;
+    }
+    return REWL_OK;
+}
+
+extern "C" int rewl_batch_enqueue(rewl_batch_t *b)
+{
+    if (!b) return REWL_E_INVALID;
+    const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) return fail(nullptr, REWL_E_CUDA, "batch launch: %s", cudaGetErrorString(e));
+    for (rewl_t *h : b->runs) h->host_cycle += b->k;
+    return REWL_OK;
+}
+
+extern "C" int rewl_batch_destroy(rewl_batch_t *b)
+{
+    batch_free(b);
+    return REWL_OK;
+}

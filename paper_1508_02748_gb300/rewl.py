@@ -73,6 +73,11 @@ SIGNATURES = {
     "rewl_last_error": (ctypes.c_char_p, [_P]),
     "rewl_destroy": (ctypes.c_int, [_P]),
     "rewl_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P]),
+    "rewl_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "rewl_batch_cycles_per_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "rewl_batch_run_cycles": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "rewl_batch_enqueue": (ctypes.c_int, [_P]),
+    "rewl_batch_destroy": (ctypes.c_int, [_P]),
     "rewl_join_noalloc": (ctypes.c_int, [ctypes.POINTER(rewl_config), _P, _P, _P, _P]),
     "rewl_noalloc_last_error": (ctypes.c_char_p, []),
 }
@@ -279,3 +284,44 @@ def philox(counters, key) -> "object":
                                       ctypes.c_void_p(out.data_ptr()), c.shape[0],
                                       ctypes.c_void_p(s.cuda_stream)))
     return out
+
+
+class Batch:
+    """Several REWL runs advanced together by one CUDA graph (rewl_batch_*).
+
+    The runs sample concurrently on the GPU; each keeps exactly the trajectory
+    it would have alone.  Keep the runs alive while the batch exists and do
+    not drive them individually meanwhile."""
+
+    def __init__(self, runs, stream=None):
+        import torch
+        self.runs = list(runs)
+        lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.runs[0].device)
+        arr = (ctypes.c_void_p * len(self.runs))(*[r._h.value for r in self.runs])
+        h = ctypes.c_void_p(0)
+        rc = lib.rewl_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.runs),
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _check(rc, None)
+        self._h = h
+        k = ctypes.c_uint64(0)
+        _check(lib.rewl_batch_cycles_per_launch(self._h, ctypes.byref(k)))
+        self.k = int(k.value)
+
+    def run_cycles(self, n: int):
+        _check(load_library().rewl_batch_run_cycles(self._h, n), None)
+
+    def enqueue(self):
+        """Queues one graph launch (self.k cycles of every run) without waiting."""
+        _check(load_library().rewl_batch_enqueue(self._h), None)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().rewl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -52,4 +52,21 @@ REWL_L32 = Workload("rewl_L32_16x4_w32", 32, 16, 4, 0.75, 0.75, 32, 1.0, 1e-6, 0
 # Precision study: L=64, 32x8 windows at 75% overlap, 16 walkers per window, ln f down to 1e-8.
 REWL_L64 = Workload("rewl_L64_32x8_w16", 64, 32, 8, 0.75, 0.75, 16, 1.0, 1e-8, 0.5, 0.8, 10_000, 16, 4)
 
+# Uneven batch: 24 independent REWL runs, six each of L = 16, 24, 32, 48 with
+# window grids and walkers per window scaled to L (4x2/32, 8x2/16, 12x4/16,
+# 16x4/8; 10,752 walkers in all), 75% overlap, ln f down to 1e-6.
+BATCH_SPECS = ((16, 4, 2, 32), (24, 8, 2, 16), (32, 12, 4, 16), (48, 16, 4, 8))
+
+
+def mixed_batch() -> list:
+    out = []
+    for L, nE, nM, W in BATCH_SPECS:
+        for r in range(6):
+            out.append(Workload(f"batch_L{L}_{nE}x{nM}_w{W}_r{r}", L, nE, nM, 0.75, 0.75, W, 1.0, 1e-6, 0.5, 0.8,
+                                10_000, 8, 5))
+    return out
+
+
+BATCH_NAME = "batch_24_mixed_L16_24_32_48"
+
 ALL = {w.name: w for w in (SERIAL_L4, REWL_L8, REWL_L32, REWL_L64)}
