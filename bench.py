@@ -63,7 +63,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
-    ap.add_argument("--precision", default=None, choices=["fp64", "f32x2"],
+    ap.add_argument("--no-autotune", action="store_true", help="use the default tiling")
+    ap.add_argument("--lnf-final", type=float, default=None, help="override the workload's final ln f")
+    ap.add_argument("--precision", default=None, choices=["fp64", "f32x2", "f32"],
                     help="ln g tables (default: the workload's: fp64)")
     ap.add_argument("--sampler", default="warp", choices=["warp", "thread"])
     ap.add_argument("--time-to", action="store_true",
@@ -258,10 +260,15 @@ def run_gpu(args, w):
             import torch.distributed as dist
             dist.barrier()
 
-    prec = {"fp64": P.FP64, "f32x2": P.F32X2}[args.precision]
+    prec = {"fp64": P.FP64, "f32x2": P.F32X2, "f32": P.F32}[args.precision]
     smp = {"warp": P.SAMPLER_WARP, "thread": P.SAMPLER_THREAD}[args.sampler]
+    if args.lnf_final is not None:
+        w = w.with_(lnf_final=args.lnf_final)
     cfg = P.Config.from_workload(w, replicate=replica_seed_index(rank), drive_budget=10**8, precision=prec,
                                  sampler=smp)
+    if not args.no_autotune and args.sampler == "warp":
+        from paper_1508_02748_gb300.autotune import autotune
+        cfg = autotune(cfg, device=str(dev))
     if args.time_to:
         return run_time_to(args, w, cfg, dev)
     run = P.REWL(cfg, device=str(dev))
@@ -343,10 +350,12 @@ def run_gpu(args, w):
         cpu = None if args.no_cpu else oracle_rate(w, args.cpu_seconds)
         line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2"}[args.precision],
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
                 "data": "synthetic",
-                "config": _config_dict(w, "flushed between steps (256 MiB write, outside the step events)",
-                                       args.precision, args.sampler),
+                "config": dict(_config_dict(w, "flushed between steps (256 MiB write, outside the step events)",
+                                            args.precision, args.sampler),
+                               tiling={"sampler": cfg.sampler, "lanes_per_walker": cfg.lanes_per_walker,
+                                       "walkers_per_block": cfg.walkers_per_block}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
                 "clocks": clk,
                 "run": {"iteration": st["iteration"], "lnf": st["lnf"], "exch_accepts": st["exch_accepts"],
@@ -380,7 +389,7 @@ def run_time_to(args, w, cfg, dev):
         ok = np.isfinite(ex) & (ex > 0) & np.isfinite(mE)
         eps = float(np.mean(np.abs(mE[ok] - ex[ok]) / ex[ok]))
     line = {"metric": "time-to-ln f<=%g" % w.lnf_final, "value": elapsed, "unit": "s",
-            "higher_is_better": False, "n_gpus": 1, "dtype": {"fp64": "f64", "f32x2": "f32x2"}[args.precision],
+            "higher_is_better": False, "n_gpus": 1, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
             "data": "synthetic", "config": _config_dict(w, "n/a", args.precision, args.sampler),
             "iterations": st["iteration"], "cycles": st["cycles"], "trials_per_walker": st["trials"],
             "lnf_final": st["lnf"], "mean_eps_E_marginal_vs_exact": eps,
@@ -405,11 +414,35 @@ def run_gpu_batch(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    prec = {"fp64": P.FP64, "f32x2": P.F32X2}[args.precision]
+    prec = {"fp64": P.FP64, "f32x2": P.F32X2, "f32": P.F32}[args.precision]
     wl = workloads.mixed_batch()
-    runs = [P.REWL(P.Config.from_workload(w, replicate=i + 24 * replica_seed_index(rank), drive_budget=10**8,
-                                          precision=prec), device=str(dev)) for i, w in enumerate(wl)]
-    batch = P.Batch(runs)
+
+    def make(lanes):
+        rs = [P.REWL(P.Config.from_workload(w, replicate=i + 24 * replica_seed_index(rank), drive_budget=10**8,
+                                            precision=prec, lanes_per_walker=lanes), device=str(dev))
+              for i, w in enumerate(wl)]
+        return rs, P.Batch(rs)
+
+    lanes_best, tune = 0, {}
+    if not args.no_autotune:
+        # the tiling does not change any run's trajectory; time one launch per choice
+        for lanes in (32, 16, 8):
+            rs, bt = make(lanes)
+            with torch.cuda.stream(bt.stream):
+                bt.enqueue()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(bt.stream)
+                bt.enqueue()
+                e1.record(bt.stream)
+            bt.stream.synchronize()
+            tune[lanes] = e0.elapsed_time(e1)
+            bt.close()
+            for r in rs:
+                r.close()
+            del rs, bt
+            torch.cuda.empty_cache()
+        lanes_best = min(tune, key=tune.get)
+    runs, batch = make(lanes_best)
     s = batch.stream
     active = sum(r.status()["n_walkers"] for r in runs)
     trials_per_step = batch.k * wl[0].exchange_interval * active
@@ -450,9 +483,11 @@ def run_gpu_batch(args):
             cpu["sample"] += " (the L=16 member of the batch, as the per-trial CPU cost)"
         line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2"}[args.precision],
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": workloads.BATCH_NAME, "runs": len(runs), "walkers": active,
+                           "tiling": {"lanes_per_walker": lanes_best or "auto",
+                                      "tried_ms_per_launch": {str(k): v for k, v in tune.items()}},
                            "L": [16, 24, 32, 48], "cycles_per_step": batch.k, "ln_g": args.precision,
                            "sampler": "warp", "l2": "flushed between steps (256 MiB write, outside the step events)"},
                 "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
