@@ -14,7 +14,7 @@ import dataclasses
 import json
 import os
 
-from .rewl import FP64, REWL, SAMPLER_THREAD, SAMPLER_WARP, Config
+from .rewl import FP64, REWL, SAMPLER_THREAD, SAMPLER_WARP, Config, REWLError
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
@@ -49,16 +49,22 @@ def autotune(cfg: Config, device: str = "cuda:0", cycles: int = 2, cache_path: s
     best = None
     for sampler, lanes, wpb in candidates(cfg):
         trial = dataclasses.replace(cfg, sampler=sampler, lanes_per_walker=lanes, walkers_per_block=wpb)
-        run = REWL(trial, device=device)
-        with torch.cuda.stream(run.stream):
-            run.enqueue_cycle()
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record(run.stream)
-            for _ in range(cycles):
+        try:
+            run = REWL(trial, device=device)
+            with torch.cuda.stream(run.stream):
                 run.enqueue_cycle()
-            t1.record(run.stream)
-        run.stream.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(run.stream)
+                for _ in range(cycles):
+                    run.enqueue_cycle()
+                t1.record(run.stream)
+            run.stream.synchronize()
+            run.status()                    # surfaces a failed launch
+        except REWLError as err:            # a tiling this shape cannot use
+            if verbose:
+                print(f"autotune {key}: sampler={sampler} lanes={lanes} wpb={wpb}: skipped ({err})", flush=True)
+            continue
         ms = t0.elapsed_time(t1) / cycles
         if verbose:
             print(f"autotune {key}: sampler={sampler} lanes={lanes} wpb={wpb}: {ms:.3f} ms/cycle", flush=True)

@@ -488,6 +488,10 @@ cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int 
     const size_t per = tree_smem_per_warp(p, smt);
     const int gpw = 32 / group;
     if (warps <= 0) warps = smt ? 1 : 4;
+    // no more warps per block than the shared memory of one block holds
+    const size_t max_smem = 227 * 1024;
+    while (warps > 1 && per * (size_t)gpw * warps > max_smem) --warps;
+    if (per * (size_t)gpw * warps > max_smem) return cudaErrorInvalidValue;
     const size_t smem = per * (size_t)gpw * warps;
     const int walkers_per_block = gpw * warps;
     const int blocks = (p.nwalk + walkers_per_block - 1) / walkers_per_block;
