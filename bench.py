@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tiling")
     ap.add_argument("--lnf-final", type=float, default=None, help="override the workload's final ln f")
+    ap.add_argument("--max-seconds", type=float, default=300.0,
+                    help="--time-to: stop (and report the iteration reached) after this wall time")
     ap.add_argument("--precision", default=None, choices=["fp64", "f32x2", "f32"],
                     help="ln g tables (default: the workload's: fp64)")
     ap.add_argument("--sampler", default="warp", choices=["warp", "thread"])
@@ -379,10 +381,17 @@ def run_time_to(args, w, cfg, dev):
     t0 = time.perf_counter()
     st = run.status()
     chunk = 64 * w.check_every
+    capped = False
     while not st["done"]:
         st = run.run_cycles(chunk)
+        if time.perf_counter() - t0 > args.max_seconds:
+            capped = True
+            break
     elapsed = time.perf_counter() - t0
-    mE = run.lng(P.LNG_MARGINAL_E)
+    try:
+        mE = run.lng(P.LNG_MARGINAL_E)
+    except P.REWLError:               # a capped run may not have pieces to join yet
+        mE = np.full(w.N + 1, np.nan)
     ex = exact_lngE(w.L)
     eps = None
     if ex is not None:
@@ -391,6 +400,7 @@ def run_time_to(args, w, cfg, dev):
     line = {"metric": "time-to-ln f<=%g" % w.lnf_final, "value": elapsed, "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
             "data": "synthetic", "config": _config_dict(w, "n/a", args.precision, args.sampler),
+            "capped": capped, "max_seconds": args.max_seconds,
             "iterations": st["iteration"], "cycles": st["cycles"], "trials_per_walker": st["trials"],
             "lnf_final": st["lnf"], "mean_eps_E_marginal_vs_exact": eps,
             "exchange_acceptance": st["exch_accepts"] / max(1, st["exch_attempts"])}
