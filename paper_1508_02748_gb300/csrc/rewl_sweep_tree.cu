@@ -310,22 +310,45 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         const int pack = (de_own + 2) | ((dm_own + 1) << 3);
 
         // ---- 2. the history's earlier trials: moves from the lanes that took them
-        // (a history that accepts a move out of the window is never the true
-        // path; its bins are clamped below only to keep its reads in bounds)
-        box->move[gl] = pack;
-        __syncwarp(gmask);
+        // (shared lattice) or recomputed (register lattice); a history that
+        // accepts a move out of the window is never the true path, and its
+        // bins are clamped below only to keep its reads in bounds
         int ce = e, cm = m, cbin = ci;
         int vb[DEPTH];               // bin after each earlier trial (-1 past the own depth)
-        #pragma unroll
-        for (int k = 0; k < DEPTH; ++k) {
-            const int pk = box->move[srck[k]];
-            if (k < dl && ((hist >> k) & 1)) {
-                const int de = (pk & 7) - 2, dm = ((pk >> 3) & 3) - 1;
-                ce += de;
-                cm += dm;
-                cbin += de * wM + dm;
+        if (REG) {
+            // register lattice: recompute the moves the history accepts (the
+            // lattice under the history's earlier flips), no exchange needed
+            unsigned long long Fk = 0;
+            #pragma unroll
+            for (int k = 0; k < DEPTH; ++k) {
+                if (k < dl && ((hist >> k) & 1)) {
+                    const unsigned long long v = lat64 ^ Fk;
+                    const uint32_t a = sa[k];
+                    const uint32_t sk = (uint32_t)(v >> (a & 63u)) & 1u;
+                    const int nk = (int)(((uint32_t)(v >> ((a >> 6) & 63u)) & 1u) + ((uint32_t)(v >> ((a >> 12) & 63u)) & 1u)
+                                       + ((uint32_t)(v >> ((a >> 18) & 63u)) & 1u) + ((uint32_t)(v >> ((a >> 24) & 63u)) & 1u));
+                    const int de = sk ? nk - 2 : 2 - nk, dm = sk ? -1 : 1;
+                    ce += de;
+                    cm += dm;
+                    cbin += de * wM + dm;
+                    Fk ^= 1ull << (a & 63u);
+                }
+                vb[k] = k < dl ? cbin : -1;
             }
-            vb[k] = k < dl ? cbin : -1;
+        } else {
+            box->move[gl] = pack;
+            __syncwarp(gmask);
+            #pragma unroll
+            for (int k = 0; k < DEPTH; ++k) {
+                const int pk = box->move[srck[k]];
+                if (k < dl && ((hist >> k) & 1)) {
+                    const int de = (pk & 7) - 2, dm = ((pk >> 3) & 3) - 1;
+                    ce += de;
+                    cm += dm;
+                    cbin += de * wM + dm;
+                }
+                vb[k] = k < dl ? cbin : -1;
+            }
         }
 
         // ---- 3. decision of the own trial (Eq. 1)
