@@ -181,6 +181,31 @@ int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t *host_H, si
 int rewl_get_lng(rewl_t *h, int what, double *host_out, size_t capacity, size_t *needed,
                  int32_t *host_ematch, int32_t *host_mmatch);
 
+/* Jackknife over the walkers of each window (Sec. 2: "jackknifing ... to
+ * compute the statistical errors from a unique production run"): replicate k
+ * (k = 0..W-1) is the merge / join / normalisation of rewl_get_lng without
+ * walker k of every window; host_mean gets the mean of the W replicates and
+ * host_err sqrt((W-1)/W * sum_k (replicate_k - mean)^2), per entry, for
+ * what = REWL_LNG_JOINED ((N+1)^2 entries) or REWL_LNG_MARGINAL_E (N+1).
+ * Entries missing from any replicate: mean -inf, error NaN.  Needs
+ * walkers_per_window >= 2.  Errors as rewl_get_lng. */
+int rewl_get_lng_jackknife(rewl_t *h, int what, double *host_mean, double *host_err, size_t capacity,
+                           size_t *needed);
+
+/* Checkpoint / resume.  rewl_save writes the whole state of a run
+ * (configuration, walkers' spins, bins and trial counters, ln g and H tables,
+ * iteration, ln f, exchange and cycle counters) to the host file `path`.
+ * rewl_load restores it into a new handle on a caller-provided workspace of
+ * at least rewl_workspace_size() bytes for the saved configuration
+ * (rewl_checkpoint_config reads that configuration from the file first).
+ * Every random draw is a Philox counter of the trial or exchange index, so a
+ * restored run continues exactly as the saved one would have.  The file is
+ * host-endian and tied to this library version.  Errors: REWL_E_INVALID
+ * (I/O, wrong file), REWL_E_CAPACITY, REWL_E_CUDA. */
+int rewl_save(rewl_t *h, const char *path);
+int rewl_checkpoint_config(const char *path, rewl_config *cfg);
+int rewl_load(const char *path, void *d_workspace, size_t workspace_bytes, void *stream, rewl_t **out);
+
 /* Message of the last failing call on h (never NULL). */
 const char *rewl_last_error(const rewl_t *h);
 

@@ -73,6 +73,8 @@ def lib():
             L.orc_set_tables.argtypes = [P, P, P]
             L.orc_join.argtypes = [P, P, P, P]
             L.orc_join.restype = i32
+            L.orc_join_excl.argtypes = [P, i32, P, P, P]
+            L.orc_join_excl.restype = i32
             L.orc_marginal_e.argtypes = [i32, P, P]
             L.orc_bin_possible.argtypes = [i32, i32, i32]
             L.orc_bin_possible.restype = i32
@@ -233,6 +235,46 @@ class OracleREWL:
         if rc:
             raise RuntimeError(f"oracle join failed: code {rc}")
         return out, em, mm
+
+
+def jackknife_replicates(run: "OracleREWL", marginal: bool = False) -> np.ndarray:
+    """Replicate k (k = 0..W-1) is the join of the run without walker k of
+    every window (the jackknife over walkers of Sec. 2); marginal=True gives
+    each replicate's E marginal (Eq. 3) instead of the joint table."""
+    B = run.N + 1
+    c = run.cfg
+    em = np.zeros(max(1, c.n_win_M * max(1, c.n_win_E - 1)), dtype=np.int32)
+    mm = np.zeros(max(1, c.n_win_M - 1), dtype=np.int32)
+    reps = []
+    for k in range(c.walkers_per_window):
+        out = np.zeros((B, B), dtype=np.float64)
+        rc = lib().orc_join_excl(run._h, k, _ptr(out), _ptr(em), _ptr(mm))
+        if rc:
+            raise RuntimeError(f"oracle jackknife join failed: code {rc}")
+        reps.append(marginal_e(out) if marginal else out)
+    return np.stack(reps)
+
+
+def jackknife_stats(R: np.ndarray):
+    """Jackknife mean and error of replicates R (W x ...): mean = average,
+    error = sqrt((W-1)/W * sum_k (R_k - mean)^2), per entry; entries missing
+    from any replicate get mean -inf and error NaN.  Differences are taken
+    from the first replicate to keep the sums small."""
+    W = R.shape[0]
+    ok = np.all(np.isfinite(R), axis=0)
+    ref = np.where(ok, R[0], 0.0)
+    d = np.where(ok, R - ref, 0.0)
+    s1 = d.sum(axis=0)
+    s2 = (d * d).sum(axis=0)
+    mean = np.where(ok, ref + s1 / W, -np.inf)
+    var = (W - 1) / W * (s2 - s1 * s1 / W)
+    err = np.where(ok, np.sqrt(np.maximum(var, 0.0)), np.nan)
+    return mean, err
+
+
+def jackknife(run: "OracleREWL", marginal: bool = False):
+    """Jackknife mean and error of ln g over the walkers of each window."""
+    return jackknife_stats(jackknife_replicates(run, marginal))
 
 
 def marginal_e(lng_joint: np.ndarray) -> np.ndarray:

@@ -547,26 +547,30 @@ static double logsumexp(const double *v, size_t n, size_t stride)
 }
 
 /* Walkers of one window merged into one table: each walker is shifted by the
- * mean, over the bins every walker visited, of its difference to walker 0;
- * each bin is the mean over the walkers that visited it; -inf if none did. */
-static int merge_window(const orc_rewl *s, int win, double *out)
+ * mean, over the bins every walker visited, of its difference to the first
+ * walker; each bin is the mean over the walkers that visited it; -inf if none
+ * did.  Walker `excl` of the window (-1: none) is left out entirely (the
+ * jackknife replicates of Sec. 2). */
+static int merge_window(const orc_rewl *s, int win, double *out, int excl)
 {
     int W = s->W;
+    int ref = excl == 0 ? 1 : 0;
     size_t n = tsize(s, win);
     double *off = (double *)calloc(W, sizeof(double));
     size_t common = 0;
     for (size_t i = 0; i < n; ++i) {
         int all = 1;
-        for (int k = 0; k < W; ++k) if (s->H[s->toff[win * W + k] + i] < 0) { all = 0; break; }
+        for (int k = 0; k < W; ++k) if (k != excl && s->H[s->toff[win * W + k] + i] < 0) { all = 0; break; }
         common += all;
     }
-    if (W > 1 && common == 0) { free(off); return ORC_E_JOIN; }
-    for (int k = 1; k < W; ++k) {
+    if (W - (excl >= 0) > 1 && common == 0) { free(off); return ORC_E_JOIN; }
+    for (int k = 0; k < W; ++k) {
+        if (k == ref || k == excl) continue;
         double acc = 0.0;
-        const double *g0 = s->lng + s->toff[win * W], *gk = s->lng + s->toff[win * W + k];
+        const double *g0 = s->lng + s->toff[win * W + ref], *gk = s->lng + s->toff[win * W + k];
         for (size_t i = 0; i < n; ++i) {
             int all = 1;
-            for (int q = 0; q < W; ++q) if (s->H[s->toff[win * W + q] + i] < 0) { all = 0; break; }
+            for (int q = 0; q < W; ++q) if (q != excl && s->H[s->toff[win * W + q] + i] < 0) { all = 0; break; }
             if (all) acc += gk[i] - g0[i];
         }
         off[k] = acc / (double)common;
@@ -575,6 +579,7 @@ static int merge_window(const orc_rewl *s, int win, double *out)
         double acc = 0.0;
         int cnt = 0;
         for (int k = 0; k < W; ++k) {
+            if (k == excl) continue;
             size_t j = s->toff[win * W + k] + i;
             if (s->H[j] < 0) continue;
             acc += s->lng[j] - off[k];
@@ -615,8 +620,18 @@ static int match_point(const double *Ga, const double *Gb, int lo, int hi, int f
  * order, -inf where no walker visited, normalised so sum g = 2^N.
  * ematch: nM x (nE-1) E matching points (-1 where unused);
  * mmatch: (nM-1) M matching points. */
+int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int32_t *mmatch);
+
 int orc_join(const orc_rewl *s, double *out, int32_t *ematch, int32_t *mmatch)
 {
+    return orc_join_excl(s, -1, out, ematch, mmatch);
+}
+
+/* The join with walker `excl` of every window left out of the merge (-1:
+ * none); excl >= 0 needs at least two walkers per window. */
+int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int32_t *mmatch)
+{
+    if (excl >= s->W || (excl >= 0 && s->W < 2)) return ORC_E_INVALID;
     int N = s->N, B = N + 1, nE = s->nE, nM = s->nM;
     for (size_t i = 0; i < (size_t)B * B; ++i) out[i] = -INFINITY;
     double **piece = (double **)calloc(s->nwin, sizeof(double *));
@@ -624,7 +639,7 @@ int orc_join(const orc_rewl *s, double *out, int32_t *ematch, int32_t *mmatch)
     for (int w = 0; w < s->nwin; ++w) {
         if (!s->active[w]) continue;
         piece[w] = (double *)malloc(sizeof(double) * tsize(s, w));
-        if (merge_window(s, w, piece[w]) != ORC_OK) rc = ORC_E_JOIN;
+        if (merge_window(s, w, piece[w], excl) != ORC_OK) rc = ORC_E_JOIN;
     }
     for (int i = 0; i < nM * (nE > 1 ? nE - 1 : 1); ++i) ematch[i] = -1;
     for (int i = 0; i < (nM > 1 ? nM - 1 : 1); ++i) mmatch[i] = -1;

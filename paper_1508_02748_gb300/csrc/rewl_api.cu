@@ -30,6 +30,7 @@ struct rewl_s {
     cudaGraphExec_t graph;           // check_every cycles, the last one checking
     bool graph_ok;
     int first_active;                // a walker of a non-empty window (-1 if none)
+    double *jk_mean, *jk_err;        // jackknife results (device)
 };
 
 namespace {
@@ -107,6 +108,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     size_t st, rect, active, spins, we, wm, wt, wflat, lng, H;
     size_t piece, off, GE, eshift, efrom, eto, ematch, rowok, F, mshift, mfrom, mto, mmatch, J, red, marg, gbuf;
+    size_t jk_ref, jk_sum, jk_sq, jk_mean, jk_err;
     size_t fail, total;
 };
 
@@ -187,6 +189,11 @@ Layout layout_of(const Dims &d)
     L.red = take(8 * 2048);
     L.marg = take(8 * B);
     L.gbuf = take(8 * 2 * B * (size_t)d.nM);
+    L.jk_ref = take(8 * B * B);
+    L.jk_sum = take(8 * B * B);
+    L.jk_sq = take(8 * B * B);
+    L.jk_mean = take(8 * B * B);
+    L.jk_err = take(8 * B * B);
     L.fail = take(4);
     L.total = o;
     return L;
@@ -307,8 +314,12 @@ extern "C" int rewl_workspace_size(const rewl_config *cfg, size_t *bytes)
     return REWL_OK;
 }
 
-extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_workspace,
-                           size_t workspace_bytes, void *stream, rewl_t **out)
+namespace {
+
+// Handle setup; `initialise` draws the spins and drives the walkers (a
+// restored run gets its state from a checkpoint instead).
+int create_impl(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_workspace, size_t workspace_bytes,
+                void *stream, rewl_t **out, bool initialise)
 {
     const char *why = nullptr;
     int rc = check_config(cfg, &why);
@@ -344,6 +355,7 @@ extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spin
     p.lnf_final = cfg->lnf_final; p.lnf_factor = cfg->lnf_factor;
     p.flat_q = (long long)std::llround(cfg->flatness * 1e6);
     p.drive_budget = cfg->drive_budget;
+    p.join_exclude = -1;
     p.rect = (const int4 *)(base + lay.rect);
     p.active = (const int32_t *)(base + lay.active);
     p.spins = (uint32_t *)(base + lay.spins);
@@ -374,6 +386,11 @@ extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spin
     j.red = (double *)(base + lay.red);
     j.marg = (double *)(base + lay.marg);
     j.gbuf = (double *)(base + lay.gbuf);
+    j.jk_ref = (double *)(base + lay.jk_ref);
+    j.jk_sum = (double *)(base + lay.jk_sum);
+    j.jk_sq = (double *)(base + lay.jk_sq);
+    h->jk_mean = (double *)(base + lay.jk_mean);
+    h->jk_err = (double *)(base + lay.jk_err);
     h->d_fail = (int32_t *)(base + lay.fail);
     h->d_stage = (uint8_t *)(base + lay.J);
 
@@ -425,6 +442,11 @@ extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spin
     CKB(cudaMemsetAsync(p.lng, 0, 8 * (size_t)d.nwalk * d.tstride, h->stream));
     CKB(cudaMemsetAsync(p.H, 0xFF, 4 * (size_t)d.nwalk * d.tstride, h->stream));
     CKB(cudaMemsetAsync(h->d_fail, 0, 4, h->stream));
+    if (!initialise) {
+        CKB(cudaStreamSynchronize(h->stream));
+        *out = h;
+        return REWL_OK;
+    }
     const uint8_t *d_bytes = nullptr;
     if (host_init_spins) {
         CKB(cudaMemcpyAsync(h->d_stage, host_init_spins, (size_t)d.nwalk * d.N, cudaMemcpyHostToDevice, h->stream));
@@ -441,6 +463,133 @@ extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spin
              (unsigned long long)cfg->drive_budget);
         return bail(REWL_E_UNREACHABLE);
     }
+    *out = h;
+    return REWL_OK;
+}
+
+}  // namespace
+
+extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_workspace,
+                           size_t workspace_bytes, void *stream, rewl_t **out)
+{
+    return create_impl(cfg, host_init_spins, d_workspace, workspace_bytes, stream, out, true);
+}
+
+// ------------------------------------------------------------- checkpoint ----
+
+namespace {
+
+const char kCkptMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '1'};
+
+struct CkptFile {
+    FILE *f = nullptr;
+    ~CkptFile() { if (f) fclose(f); }
+};
+
+// Device <-> file in chunks through one host buffer.
+int dev_to_file(rewl_t *h, FILE *f, const void *dev, size_t bytes, std::vector<unsigned char> &buf)
+{
+    for (size_t o = 0; o < bytes; o += buf.size()) {
+        const size_t n = std::min(buf.size(), bytes - o);
+        CK(h, cudaMemcpyAsync(buf.data(), (const unsigned char *)dev + o, n, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (fwrite(buf.data(), 1, n, f) != n) return fail(h, REWL_E_INVALID, "checkpoint write failed");
+    }
+    return REWL_OK;
+}
+
+int file_to_dev(rewl_t *h, FILE *f, void *dev, size_t bytes, std::vector<unsigned char> &buf)
+{
+    for (size_t o = 0; o < bytes; o += buf.size()) {
+        const size_t n = std::min(buf.size(), bytes - o);
+        if (fread(buf.data(), 1, n, f) != n) return fail(h, REWL_E_INVALID, "checkpoint truncated");
+        CK(h, cudaMemcpyAsync((unsigned char *)dev + o, buf.data(), n, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return REWL_OK;
+}
+
+struct StateRegion {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<StateRegion> state_regions(rewl_t *h)
+{
+    const Params &p = h->p;
+    const size_t tab = (size_t)p.nwalk * (size_t)p.tstride;
+    return {{p.st, sizeof(DevState)},
+            {p.spins, 4 * (size_t)p.nwords * p.nwalk},
+            {p.we, 4 * (size_t)p.nwalk},
+            {p.wm, 4 * (size_t)p.nwalk},
+            {p.wt, 8 * (size_t)p.nwalk},
+            {p.wflat, 4 * (size_t)p.nwalk},
+            {p.lng, 8 * tab},
+            {p.H, 4 * tab}};
+}
+
+}  // namespace
+
+extern "C" int rewl_save(rewl_t *h, const char *path)
+{
+    if (!h || !path) return REWL_E_INVALID;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CkptFile cf;
+    cf.f = fopen(path, "wb");
+    if (!cf.f) return fail(h, REWL_E_INVALID, "cannot open %s for writing", path);
+    const uint32_t version = 1, csize = (uint32_t)sizeof(rewl_config);
+    const unsigned long long hc = h->host_cycle;
+    if (fwrite(kCkptMagic, 1, 8, cf.f) != 8 || fwrite(&version, 4, 1, cf.f) != 1 || fwrite(&csize, 4, 1, cf.f) != 1 ||
+        fwrite(&h->cfg, sizeof(rewl_config), 1, cf.f) != 1 || fwrite(&hc, 8, 1, cf.f) != 1)
+        return fail(h, REWL_E_INVALID, "checkpoint write failed");
+    std::vector<unsigned char> buf((size_t)64 << 20);
+    for (const StateRegion &r : state_regions(h)) {
+        const int rc = dev_to_file(h, cf.f, r.dev, r.bytes, buf);
+        if (rc) return rc;
+    }
+    return REWL_OK;
+}
+
+extern "C" int rewl_checkpoint_config(const char *path, rewl_config *cfg)
+{
+    if (!path || !cfg) return fail(nullptr, REWL_E_INVALID, "null argument");
+    CkptFile cf;
+    cf.f = fopen(path, "rb");
+    if (!cf.f) return fail(nullptr, REWL_E_INVALID, "cannot open %s", path);
+    char magic[8];
+    uint32_t version = 0, csize = 0;
+    if (fread(magic, 1, 8, cf.f) != 8 || std::memcmp(magic, kCkptMagic, 8) != 0 || fread(&version, 4, 1, cf.f) != 1 ||
+        fread(&csize, 4, 1, cf.f) != 1 || version != 1 || csize != sizeof(rewl_config) ||
+        fread(cfg, sizeof(rewl_config), 1, cf.f) != 1)
+        return fail(nullptr, REWL_E_INVALID, "%s is not a librewl checkpoint of this version", path);
+    return REWL_OK;
+}
+
+extern "C" int rewl_load(const char *path, void *d_workspace, size_t workspace_bytes, void *stream, rewl_t **out)
+{
+    rewl_config cfg;
+    int rc = rewl_checkpoint_config(path, &cfg);
+    if (rc) return rc;
+    CkptFile cf;
+    cf.f = fopen(path, "rb");
+    if (!cf.f) return fail(nullptr, REWL_E_INVALID, "cannot open %s", path);
+    if (fseek(cf.f, 16 + (long)sizeof(rewl_config), SEEK_SET) != 0)
+        return fail(nullptr, REWL_E_INVALID, "checkpoint truncated");
+    unsigned long long hc = 0;
+    if (fread(&hc, 8, 1, cf.f) != 1) return fail(nullptr, REWL_E_INVALID, "checkpoint truncated");
+    rewl_t *h = nullptr;
+    rc = create_impl(&cfg, nullptr, d_workspace, workspace_bytes, stream, &h, false);
+    if (rc) return rc;
+    std::vector<unsigned char> buf((size_t)64 << 20);
+    for (const StateRegion &r : state_regions(h)) {
+        rc = file_to_dev(h, cf.f, r.dev, r.bytes, buf);
+        if (rc) {
+            fail(nullptr, rc, "%s", h->err);
+            rewl_destroy(h);
+            return rc;
+        }
+    }
+    h->host_cycle = hc;
     *out = h;
     return REWL_OK;
 }
@@ -674,6 +823,37 @@ extern "C" int rewl_get_lng(rewl_t *h, int what, double *host_out, size_t capaci
     if (host_mmatch)
         CK(h, cudaMemcpyAsync(host_mmatch, h->j.mmatch, 4 * (size_t)(p.nM > 1 ? p.nM - 1 : 1),
                               cudaMemcpyDeviceToHost, h->stream));
+    return sync(h);
+}
+
+extern "C" int rewl_get_lng_jackknife(rewl_t *h, int what, double *host_mean, double *host_err, size_t capacity,
+                                      size_t *needed)
+{
+    if (!h) return REWL_E_INVALID;
+    const Params &p0 = h->p;
+    const size_t B = (size_t)p0.N + 1;
+    size_t n;
+    if (what == REWL_LNG_JOINED) n = B * B;
+    else if (what == REWL_LNG_MARGINAL_E) n = B;
+    else return fail(h, REWL_E_INVALID, "unknown output kind %d", what);
+    if (needed) *needed = n;
+    if (p0.W < 2) return fail(h, REWL_E_INVALID, "the jackknife needs at least two walkers per window");
+    if (!host_mean || !host_err || capacity < n) return fail(h, REWL_E_CAPACITY, "need %zu entries", n);
+    Params p = p0;
+    for (int k = 0; k < p.W; ++k) {
+        p.join_exclude = k;
+        CK(h, cudaMemsetAsync(&p.st->join_error, 0, sizeof(int32_t), h->stream));
+        CK(h, launch_join(p, h->j, h->stream));
+        if (what == REWL_LNG_MARGINAL_E) CK(h, launch_marginal_e(p, h->j, h->stream));
+        CK(h, launch_jk_accum(h->j, what == REWL_LNG_JOINED ? h->j.J : h->j.marg, n, k, h->stream));
+        DevState ds;
+        const int rc = read_state(h, &ds);
+        if (rc) return rc;
+        if (ds.join_error) return fail(h, REWL_E_JOIN, "jackknife replicate %d: join failed (code %d)", k, ds.join_error);
+    }
+    CK(h, launch_jk_final(h->j, h->jk_mean, h->jk_err, n, p.W, h->stream));
+    CK(h, cudaMemcpyAsync(host_mean, h->jk_mean, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(host_err, h->jk_err, 8 * n, cudaMemcpyDeviceToHost, h->stream));
     return sync(h);
 }
 

@@ -78,6 +78,8 @@ struct Params {
     long long flat_q; // round(flatness * 1e6)
     uint64_t drive_budget;
 
+    int join_exclude; // merge: walker index within each window left out (-1: none)
+
     const int4 *rect;       // per window: e0, e1, m0, m1
     const int32_t *active;  // per window: 1 if it can hold a configuration
 
@@ -109,6 +111,7 @@ struct JoinScratch {
     double *red;      // reduction scratch (>= 2 * 1024 doubles)
     double *marg;     // N+1 marginal output
     double *gbuf;     // nM x 2 x (N+1) work space of the E matching chains
+    double *jk_ref, *jk_sum, *jk_sq;   // jackknife accumulators, (N+1)^2 each
 };
 
 // Kernel launchers (rewl_kernels.cu, rewl_join.cu); all return cudaError_t of the launch.
@@ -127,6 +130,8 @@ cudaError_t launch_tables_to_double(const Params &p, double *d_out, cudaStream_t
 cudaError_t launch_tables_from_double(const Params &p, const double *d_in, cudaStream_t s);
 cudaError_t launch_join(const Params &p, const JoinScratch &j, cudaStream_t s);
 cudaError_t launch_marginal_e(const Params &p, const JoinScratch &j, cudaStream_t s);
+cudaError_t launch_jk_accum(const JoinScratch &j, const double *x, size_t n, int k, cudaStream_t s);
+cudaError_t launch_jk_final(const JoinScratch &j, double *mean, double *err, size_t n, int W, cudaStream_t s);
 
 enum : int { DECIDE_XSTEP = 1, DECIDE_CYCLE = 2, DECIDE_CHECK = 4 };
 

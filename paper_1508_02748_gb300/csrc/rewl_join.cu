@@ -34,7 +34,7 @@ __device__ __forceinline__ double lng_at(const Params &p, size_t i)
 __device__ __forceinline__ bool all_seen(const Params &p, int win, int bin)
 {
     for (int k = 0; k < p.W; ++k)
-        if (p.H[(size_t)(win * p.W + k) * p.tstride + bin] < 0) return false;
+        if (k != p.join_exclude && p.H[(size_t)(win * p.W + k) * p.tstride + bin] < 0) return false;
     return true;
 }
 
@@ -76,15 +76,18 @@ __device__ int match_point(const double *Ga, const double *Gb, int lo, int hi, i
 
 }  // namespace
 
-// 1a. Offsets: one thread per (window, walker k >= 1), bins in order.
+// 1a. Offsets: one thread per (window, walker), bins in order, relative to
+// the first walker taking part (walker join_exclude, if >= 0, is left out:
+// the jackknife replicates).
 __global__ void k_merge_off(Params p, JoinScratch j)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= p.nwalk) return;
     const int win = idx / p.W, k = idx % p.W;
     if (!p.active[win]) return;
-    if (k == 0) { j.off[idx] = 0.0; return; }
-    const size_t b0 = (size_t)(win * p.W) * p.tstride, bk = (size_t)idx * p.tstride;
+    const int ref = p.join_exclude == 0 ? 1 : 0;   // the first walker taking part
+    if (k == ref || k == p.join_exclude) { j.off[idx] = 0.0; return; }
+    const size_t b0 = (size_t)(win * p.W + ref) * p.tstride, bk = (size_t)idx * p.tstride;
     double acc = 0.0;
     long long common = 0;
     for (int i = 0; i < p.T; ++i) {
@@ -108,7 +111,7 @@ __global__ void k_merge(Params p, JoinScratch j)
     int cnt = 0;
     for (int k = 0; k < p.W; ++k) {
         const size_t q = (size_t)(win * p.W + k) * p.tstride + bin;
-        if (p.H[q] < 0) continue;
+        if (k == p.join_exclude || p.H[q] < 0) continue;
         acc += lng_at(p, q) - j.off[win * p.W + k];
         ++cnt;
     }
@@ -324,6 +327,55 @@ __global__ void k_marg_out(Params p, JoinScratch j)
 cudaError_t launch_marginal_e(const Params &p, const JoinScratch &j, cudaStream_t s)
 {
     k_marg_out<<<(p.N + 1 + 127) / 128, 128, 0, s>>>(p, j);
+    return cudaGetLastError();
+}
+
+// Jackknife accumulation over replicates k = 0..W-1 (walker k left out of
+// every window's merge): differences to replicate 0 are summed; an entry that
+// is missing (-inf) in any replicate is marked NaN in jk_ref.
+__global__ void k_jk_accum(JoinScratch j, const double *x, size_t n, int k)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        if (k == 0) {
+            j.jk_ref[i] = isfinite(v) ? v : NAN;
+            j.jk_sum[i] = 0.0;
+            j.jk_sq[i] = 0.0;
+        } else if (!isfinite(v)) {
+            j.jk_ref[i] = NAN;
+        } else {
+            const double d = v - j.jk_ref[i];
+            j.jk_sum[i] += d;
+            j.jk_sq[i] += d * d;
+        }
+    }
+}
+
+__global__ void k_jk_final(JoinScratch j, double *mean, double *err, size_t n, int W)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double r = j.jk_ref[i];
+        if (isnan(r)) {
+            mean[i] = -INFINITY;
+            err[i] = NAN;
+            continue;
+        }
+        const double s1 = j.jk_sum[i], s2 = j.jk_sq[i];
+        mean[i] = r + s1 / W;
+        const double var = (double)(W - 1) / W * (s2 - s1 * s1 / W);
+        err[i] = sqrt(var > 0.0 ? var : 0.0);
+    }
+}
+
+cudaError_t launch_jk_accum(const JoinScratch &j, const double *x, size_t n, int k, cudaStream_t s)
+{
+    k_jk_accum<<<256, 256, 0, s>>>(j, x, n, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jk_final(const JoinScratch &j, double *mean, double *err, size_t n, int W, cudaStream_t s)
+{
+    k_jk_final<<<256, 256, 0, s>>>(j, mean, err, n, W);
     return cudaGetLastError();
 }
 

@@ -135,6 +135,7 @@ extern "C" int rewl_join_noalloc(const rewl_config *cfg, const double *d_lng, co
     p.wE = d.wE; p.wM = d.wM; p.T = d.T;
     p.tstride = d.T;                         // caller tables: no padding between walkers
     p.precision = REWL_FP64;
+    p.join_exclude = -1;                     // every walker takes part in the merge
     p.rect = (const int4 *)(base + o_rect);
     p.active = (const int32_t *)(base + o_act);
     p.lng = const_cast<double *>(d_lng);

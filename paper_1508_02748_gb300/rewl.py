@@ -70,6 +70,11 @@ SIGNATURES = {
     "rewl_get_tables": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t]),
     "rewl_set_tables": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t]),
     "rewl_get_lng": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _P, _P]),
+    "rewl_get_lng_jackknife": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_size_t,
+                                              ctypes.POINTER(ctypes.c_size_t)]),
+    "rewl_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "rewl_checkpoint_config": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(rewl_config)]),
+    "rewl_load": (ctypes.c_int, [ctypes.c_char_p, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "rewl_last_error": (ctypes.c_char_p, [_P]),
     "rewl_destroy": (ctypes.c_int, [_P]),
     "rewl_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P]),
@@ -260,6 +265,51 @@ class REWL:
                                            em.ctypes.data, mm.ctypes.data), self._h)
         out = out.reshape(B, B) if what == LNG_JOINED else out
         return (out, em, mm) if matches else out
+
+    def jackknife(self, what: int = LNG_JOINED):
+        """Jackknife mean and error of ln g over the walkers of each window."""
+        B = self.N + 1
+        n = B * B if what == LNG_JOINED else B
+        mean = np.zeros(n, dtype=np.float64)
+        err = np.zeros(n, dtype=np.float64)
+        need = ctypes.c_size_t(0)
+        _check(load_library().rewl_get_lng_jackknife(self._h, what, mean.ctypes.data, err.ctypes.data, n,
+                                                     ctypes.byref(need)), self._h)
+        if what == LNG_JOINED:
+            return mean.reshape(B, B), err.reshape(B, B)
+        return mean, err
+
+    def save(self, path: str):
+        """Writes a checkpoint of the whole run (rewl_save)."""
+        _check(load_library().rewl_save(self._h, os.fsencode(path)), self._h)
+
+    @classmethod
+    def load(cls, path: str, device: str = "cuda:0", stream=None) -> "REWL":
+        """Restores a run from a checkpoint into a new workspace (rewl_load)."""
+        import torch
+        lib = load_library()
+        c = rewl_config()
+        _check(lib.rewl_checkpoint_config(os.fsencode(path), ctypes.byref(c)))
+        kw = {name: getattr(c, name) for name, _ in rewl_config._fields_[1:]}
+        self = cls.__new__(cls)
+        self.cfg = Config(**kw)
+        self._c = c
+        self.device = torch.device(device)
+        nbytes = ctypes.c_size_t(0)
+        _check(lib.rewl_workspace_size(ctypes.byref(c), ctypes.byref(nbytes)))
+        self.workspace_bytes = int(nbytes.value)
+        self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        h = ctypes.c_void_p(0)
+        with torch.cuda.device(self.device):
+            rc = lib.rewl_load(os.fsencode(path), ctypes.c_void_p(self.workspace.data_ptr()), self.workspace_bytes,
+                               ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _check(rc, None)
+        self._h = h
+        self.N = self.cfg.L * self.cfg.L
+        self.n_windows = self.cfg.n_win_E * self.cfg.n_win_M
+        self.n_walkers = self.n_windows * self.cfg.walkers_per_window
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

@@ -260,3 +260,19 @@ def test_empty_windows_cycles_and_join(P, prec):
     fin = np.isfinite(Jo)
     assert np.array_equal(np.isfinite(Jg), fin)
     np.testing.assert_allclose(Jg[fin], Jo[fin], rtol=1e-12, atol=1e-9)
+
+
+@pytest.mark.parametrize("what", [0, 1])
+def test_jackknife_matches_oracle(P, what):
+    """Jackknife over walkers (Sec. 2), device vs oracle on the same run."""
+    o, g = _pair(P, L=8, n_win_E=3, n_win_M=3, walkers_per_window=4, exchange_interval=10000, seed=20152814)
+    o.run_cycles(250)
+    g.run_cycles(250)
+    _compare(o, g)
+    mo, eo = oracle.jackknife(o, marginal=(what == 1))
+    mg, eg = g.jackknife(what)
+    fin = np.isfinite(mo)
+    assert np.array_equal(np.isfinite(mg), fin)
+    np.testing.assert_allclose(mg[fin], mo[fin], rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(eg[fin], eo[fin], rtol=1e-6, atol=1e-9)
+    assert np.nanmax(eo[fin]) > 0

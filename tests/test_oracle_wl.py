@@ -311,3 +311,44 @@ def test_empty_windows_L8_6x6_geometry_and_join():
     assert np.abs(J[occ] - lg[occ]).max() < 1e-8
     r.run_cycles(3)               # sampling and exchange skip the empty windows
     assert r.info()["exch_attempt"] >= 0
+
+
+def test_jackknife_pins():
+    """Jackknife over walkers (Sec. 2): identical walkers (up to offsets) give
+    zero error and the common table; independent noise of known size gives
+    an error of that size divided by sqrt(W)."""
+    L, N, W = 6, 36, 4
+    gx = oracle.transfer_gEM(L).astype(np.float64)
+    lg = _lg(gx)
+    r = OracleREWL(OracleConfig(L=L, n_win_E=2, n_win_M=1, walkers_per_window=W, seed=9))
+    w = r.windows()
+    lng, H, toff = r.tables()
+    rng = np.random.default_rng(3)
+    T = toff[1] - toff[0]
+    for k in range(toff.size - 1):
+        e0, e1, m0, m1, _ = w[k // W]
+        blk = lg[e0:e1 + 1, m0:m1 + 1]
+        seen = np.isfinite(blk)
+        lng[toff[k]:toff[k + 1]] = np.where(seen, blk + rng.normal() * 5, 0.0).ravel()
+        H[toff[k]:toff[k + 1]] = np.where(seen, 1, -1).ravel()
+    r.set_tables(lng, H)
+    mean, err = oracle.jackknife(r)
+    occ = gx > 0
+    assert np.abs(mean[occ] - lg[occ]).max() < 1e-9
+    assert np.nanmax(err[occ]) < 1e-9
+    # With per-walker noise, every replicate's pieces carry a common shift
+    # (offsets, matching, normalisation) that cancels in a difference of two
+    # bins of the same window; for such a difference the jackknife error must
+    # equal the textbook standard error s / sqrt(W) of the walkers' values.
+    lng2 = np.where(H >= 0, lng + rng.normal(0, 0.01, size=lng.size), lng)
+    r.set_tables(lng2, H)
+    R = oracle.jackknife_replicates(r)
+    e0, e1, m0, m1, _ = w[0]
+    wm = m1 - m0 + 1
+    b1, b2 = (3, 2), (4, 3)                                  # occupied, inside window 0 only
+    assert b2[0] < w[1, 0] and occ[b1] and occ[b2]
+    y = np.array([lng2[toff[k] + (b1[0] - e0) * wm + (b1[1] - m0)] - lng2[toff[k] + (b2[0] - e0) * wm + (b2[1] - m0)]
+                  for k in range(W)])                        # walkers of window 0
+    d = R[:, b1[0], b1[1]] - R[:, b2[0], b2[1]]
+    _, err_d = oracle.jackknife_stats(d[:, None])
+    assert err_d[0] == pytest.approx(y.std(ddof=1) / math.sqrt(W), rel=1e-9)
