@@ -69,7 +69,8 @@ def parse():
                     help="--time-to: stop (and report the iteration reached) after this wall time")
     ap.add_argument("--precision", default=None, choices=["fp64", "f32x2", "f32"],
                     help="ln g tables (default: the workload's: fp64)")
-    ap.add_argument("--sampler", default="warp", choices=["warp", "thread"])
+    ap.add_argument("--sampler", default="auto", choices=["auto", "warp", "thread"],
+                    help="auto: the autotuner picks the sampler too (with --no-autotune: warp)")
     ap.add_argument("--time-to", action="store_true",
                     help="run the workload to its final ln f and report the wall time and ln g error")
     return ap.parse_args()
@@ -223,6 +224,10 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def _sampler_name(code: int) -> str:
+    return "warp" if code == 0 else "thread"
+
+
 def _config_dict(w, l2: str, precision: str = "fp64", sampler: str = "oracle") -> dict:
     return {"workload": w.name, "L": w.L, "windows": f"{w.n_win_E}x{w.n_win_M}",
             "overlap": w.overlap_E, "walkers_per_window": w.walkers_per_window,
@@ -263,14 +268,15 @@ def run_gpu(args, w):
             dist.barrier()
 
     prec = {"fp64": P.FP64, "f32x2": P.F32X2, "f32": P.F32}[args.precision]
-    smp = {"warp": P.SAMPLER_WARP, "thread": P.SAMPLER_THREAD}[args.sampler]
+    smp = {"auto": P.SAMPLER_WARP, "warp": P.SAMPLER_WARP, "thread": P.SAMPLER_THREAD}[args.sampler]
     if args.lnf_final is not None:
         w = w.with_(lnf_final=args.lnf_final)
     cfg = P.Config.from_workload(w, replicate=replica_seed_index(rank), drive_budget=10**8, precision=prec,
                                  sampler=smp)
-    if not args.no_autotune and args.sampler == "warp":
+    if not args.no_autotune:
         from paper_1508_02748_gb300.autotune import autotune
-        cfg = autotune(cfg, device=str(dev))
+        allowed = (P.SAMPLER_WARP, P.SAMPLER_THREAD) if args.sampler == "auto" else (smp,)
+        cfg = autotune(cfg, device=str(dev), samplers=allowed)
     if args.time_to:
         return run_time_to(args, w, cfg, dev)
     run = P.REWL(cfg, device=str(dev))
@@ -319,7 +325,7 @@ def run_gpu(args, w):
     achieved = OPS_PER_TRIAL * trials_per_step / sweep_s
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": achieved / peak_ops, "traffic": None,
-            "kernel": "k_sweep_tree" if args.sampler == "warp" else "k_sweep_fp64",
+            "kernel": "k_sweep_tree" if cfg.sampler == P.SAMPLER_WARP else "k_sweep_thread",
             "kernel_ms_mean": sweep_s * 1e3,
             "kernel_share_of_step": sum(sweep_ms) / total_ms,
             "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x median SM clock {mhz:.0f} MHz (derived)"}
@@ -355,7 +361,7 @@ def run_gpu(args, w):
                 "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
                 "data": "synthetic",
                 "config": dict(_config_dict(w, "flushed between steps (256 MiB write, outside the step events)",
-                                            args.precision, args.sampler),
+                                            args.precision, _sampler_name(cfg.sampler)),
                                tiling={"sampler": cfg.sampler, "lanes_per_walker": cfg.lanes_per_walker,
                                        "walkers_per_block": cfg.walkers_per_block}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
@@ -399,7 +405,7 @@ def run_time_to(args, w, cfg, dev):
         eps = float(np.mean(np.abs(mE[ok] - ex[ok]) / ex[ok]))
     line = {"metric": "time-to-ln f<=%g" % w.lnf_final, "value": elapsed, "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
-            "data": "synthetic", "config": _config_dict(w, "n/a", args.precision, args.sampler),
+            "data": "synthetic", "config": _config_dict(w, "n/a", args.precision, _sampler_name(cfg.sampler)),
             "capped": capped, "max_seconds": args.max_seconds,
             "iterations": st["iteration"], "cycles": st["cycles"], "trials_per_walker": st["trials"],
             "lnf_final": st["lnf"], "mean_eps_E_marginal_vs_exact": eps,
@@ -427,17 +433,24 @@ def run_gpu_batch(args):
     prec = {"fp64": P.FP64, "f32x2": P.F32X2, "f32": P.F32}[args.precision]
     wl = workloads.mixed_batch()
 
-    def make(lanes):
+    def make(tiling):
+        sampler, lanes, wpb = tiling
         rs = [P.REWL(P.Config.from_workload(w, replicate=i + 24 * replica_seed_index(rank), drive_budget=10**8,
-                                            precision=prec, lanes_per_walker=lanes), device=str(dev))
+                                            precision=prec, sampler=sampler, lanes_per_walker=lanes,
+                                            walkers_per_block=wpb), device=str(dev))
               for i, w in enumerate(wl)]
         return rs, P.Batch(rs)
 
-    lanes_best, tune = 0, {}
-    if not args.no_autotune:
+    choices = []
+    if args.sampler in ("auto", "warp"):
+        choices += [(P.SAMPLER_WARP, lanes, 0) for lanes in (32, 16, 8)]
+    if args.sampler in ("auto", "thread"):
+        choices += [(P.SAMPLER_THREAD, 0, wpb) for wpb in (32, 64)]
+    best, tune = choices[0], {}
+    if not args.no_autotune and len(choices) > 1:
         # the tiling does not change any run's trajectory; time one launch per choice
-        for lanes in (32, 16, 8):
-            rs, bt = make(lanes)
+        for tiling in choices:
+            rs, bt = make(tiling)
             with torch.cuda.stream(bt.stream):
                 bt.enqueue()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -445,14 +458,14 @@ def run_gpu_batch(args):
                 bt.enqueue()
                 e1.record(bt.stream)
             bt.stream.synchronize()
-            tune[lanes] = e0.elapsed_time(e1)
+            tune[tiling] = e0.elapsed_time(e1)
             bt.close()
             for r in rs:
                 r.close()
             del rs, bt
             torch.cuda.empty_cache()
-        lanes_best = min(tune, key=tune.get)
-    runs, batch = make(lanes_best)
+        best = min(tune, key=tune.get)
+    runs, batch = make(best)
     s = batch.stream
     active = sum(r.status()["n_walkers"] for r in runs)
     trials_per_step = batch.k * wl[0].exchange_interval * active
@@ -496,12 +509,17 @@ def run_gpu_batch(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": workloads.BATCH_NAME, "runs": len(runs), "walkers": active,
-                           "tiling": {"lanes_per_walker": lanes_best or "auto",
-                                      "tried_ms_per_launch": {str(k): v for k, v in tune.items()}},
+                           "tiling": {"sampler": _sampler_name(best[0]), "lanes_per_walker": best[1] or "auto",
+                                      "walkers_per_block": best[2] or "auto",
+                                      "tried_ms_per_launch": {"%s/%d/%d" % (_sampler_name(k[0]), k[1], k[2]): v
+                                                              for k, v in tune.items()}},
                            "L": [16, 24, 32, 48], "cycles_per_step": batch.k, "ln_g": args.precision,
-                           "sampler": "warp", "l2": "flushed between steps (256 MiB write, outside the step events)"},
+                           "sampler": _sampler_name(best[0]),
+                           "l2": "flushed between steps (256 MiB write, outside the step events)"},
                 "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                             "frac": achieved / peak_ops, "traffic": None, "kernel": "k_sweep_tree (24 concurrent)",
+                             "frac": achieved / peak_ops, "traffic": None,
+                             "kernel": ("k_sweep_tree" if best[0] == P.SAMPLER_WARP else "k_sweep_thread")
+                                       + " (24 concurrent)",
                              "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x median SM clock {mhz:.0f} MHz "
                                            "(derived); achieved over the whole step"},
                 "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches_per_step * K * world, "clocks": clk}

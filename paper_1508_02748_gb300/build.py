@@ -47,7 +47,8 @@ def _stale(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "rewl_internal.cuh"), os.path.join(ROOT, "include", "rewl.h"),
+    headers = [os.path.join(CSRC, "rewl_internal.cuh"), os.path.join(CSRC, "rewl_tab.cuh"),
+               os.path.join(ROOT, "include", "rewl.h"),
                os.path.abspath(__file__)]
     objs = []
     jobs = []

@@ -128,7 +128,6 @@ int check_config(const rewl_config *c, const char **why)
     if (c->check_every < 1) { *why = "check_every must be >= 1"; return REWL_E_INVALID; }
     if (c->walkers_per_block < 0 || c->walkers_per_block > 128) { *why = "walkers_per_block must be in [0, 128]"; return REWL_E_INVALID; }
     if (c->sampler != REWL_SAMPLER_WARP && c->sampler != REWL_SAMPLER_THREAD) { *why = "unknown sampler"; return REWL_E_INVALID; }
-    if (c->sampler == REWL_SAMPLER_THREAD && c->precision != REWL_FP64) { *why = "the thread sampler supports REWL_FP64 only"; return REWL_E_INVALID; }
     if (c->sampler == REWL_SAMPLER_WARP && c->walkers_per_block > 8) { *why = "warp sampler: walkers_per_block (warps per block) must be in [0, 8]"; return REWL_E_INVALID; }
     if (c->lanes_per_walker != 0 && c->lanes_per_walker != 8 && c->lanes_per_walker != 16 && c->lanes_per_walker != 32) { *why = "lanes_per_walker must be 0, 8, 16 or 32"; return REWL_E_INVALID; }
     return REWL_OK;

@@ -12,9 +12,11 @@
 //   PERM  (x, pair, i, 4)         Fisher-Yates draw i of exchange sweep x
 //   EXCH  (x, pair, k, 5)         acceptance draw of the k-th pair
 // pair = 2 * (lower window) + axis.
-#include "rewl_internal.cuh"
+#include "rewl_tab.cuh"
 
 namespace rewl {
+
+using namespace tab;
 
 namespace {
 
@@ -150,21 +152,8 @@ cudaError_t launch_drive(const Params &p, int32_t *d_fail, cudaStream_t s)
 
 // -------------------------------------------------------------- sweep ----
 
-// |x| rounded toward zero to float with integer operations only (no FP64
-// instruction): relative error below 2^-23; 0 for |x| < 2^-126; +-inf for
-// |x| >= 2^128.
-__device__ __forceinline__ float trunc_to_float(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const uint32_t hi = (uint32_t)(b >> 32);
-    const int ex = (int)((hi >> 20) & 0x7FFu);
-    if (ex < 897) return 0.0f;
-    if (ex > 1150) return __uint_as_float((hi & 0x80000000u) | 0x7F800000u);
-    const uint32_t mant = (uint32_t)(b >> 29) & 0x7FFFFFu;
-    return __uint_as_float((hi & 0x80000000u) | ((uint32_t)(ex - 896) << 23) | mant);
-}
-
-// ntrials Wang-Landau trials per walker, one thread per walker.
+// ntrials Wang-Landau trials per walker, one thread per walker (the sampler
+// for runs with many walkers, where the walkers alone fill the GPU).
 //
 // Trial t: site and u from the TRIAL stream; flipping spin s with n_up up
 // neighbours moves the bins by de = s (n_up - 2), dm = -s (s = +-1).  A
@@ -173,25 +162,31 @@ __device__ __forceinline__ float trunc_to_float(double x)
 // ln u < delta (Eq. 1 in logarithms).  Then ln g(cur) += ln f and
 // H(cur) += 1 for the bin the walker is in (Sec. 2).
 //
-// The walker's own bin is kept in registers: ln g(cur) is accumulated there
-// with the same sequence of double additions the table would see, and the
-// pending visits to H(cur) are counted; both are written back when the walker
-// leaves the bin and at the end, if it was visited (a bin left by the very
-// first trial of a launch keeps its table entries, H = -1 included).  The bin
-// proposed is never the current one (dm != 0), so the table read of
-// ln g(new) never sees a stale value.
+// The walker's own bin is kept in registers: its table value when entered
+// and the visits since; ln g(cur) = value + visits * ln f is formed exactly
+// (fma in double, a compensated float pair for REWL_F32X2) -- the same number
+// as the sequential additions whenever ln f = 2^-k -- and written back when
+// the walker leaves the bin and at the end (a bin left by the very first
+// trial of a launch keeps its entries, H = -1 included).  The bin proposed
+// is never the current one (dm != 0), so its table entry is up to date.
 //
-// The decision is screened in float: c = ln g(cur), b = ln g(new) and ln u are
-// each known to within a few float roundings (|error| < 2^-21 of their sum of
-// magnitudes), so when ln u lies farther than the margin
+// The decision is screened in float: c = ln g(cur), b = ln g(new) and ln u
+// are each known to within a few float roundings (|error| < 2^-21 of their
+// sum of magnitudes), so when ln u lies farther than
 //     M = 2^-20 (|c| + |b| + |c_0| + |ln u|) + 2^-20
-// from c - b, the float comparison gives the same answer as the exact one;
-// otherwise delta and ln u are evaluated in double.  The accept/reject
-// sequence is therefore that of the exact double comparison, while the
-// double-precision logarithm (slow on this GPU) runs only on near-ties.
-template <int WPR>
-__global__ void __launch_bounds__(128) k_sweep_fp64(Params p, unsigned long long ntrials)
+// from c - b the float comparison gives the exact answer; otherwise delta and
+// ln u are evaluated in double.  REWL_F32 (plain float, a precision
+// demonstration) compares the rounded float values directly.
+//
+// REG: the lattice (N <= 64, bit i*L + j) is one 64-bit register; otherwise
+// it lives in shared memory, word q of row r of thread t at
+// sm[(r * wpr + q) * nb + t], so the lanes of a warp never share a bank.
+template <int WPR, int PREC, bool REG>
+__global__ void __launch_bounds__(128) k_sweep_thread(Params p, unsigned long long ntrials)
 {
+    using TB = Tab<PREC>;
+    using Elem = typename TB::Elem;
+    using Val = typename TB::Val;
     extern __shared__ uint32_t sm_all[];
     const int nb = blockDim.x, tid = threadIdx.x;
     const int w = blockIdx.x * nb + tid;
@@ -199,26 +194,40 @@ __global__ void __launch_bounds__(128) k_sweep_fp64(Params p, unsigned long long
     if (!p.active[w / p.W] || p.st->done) return;
     uint32_t *sm = sm_all + tid;
     const int L = p.L, nwords = L * WPR;
-    for (int k = 0; k < nwords; ++k) sm[k * nb] = p.spins[(size_t)k * p.nwalk + w];
+    unsigned long long lat = 0;
+    if (REG) {
+        for (int r = 0; r < L; ++r) lat |= (unsigned long long)p.spins[(size_t)r * p.nwalk + w] << (r * L);
+    } else {
+        for (int k = 0; k < nwords; ++k) sm[k * nb] = p.spins[(size_t)k * p.nwalk + w];
+    }
 
     const int4 R = p.rect[w / p.W];
     const int wM = p.wM;
-    double *lng = p.lng + (size_t)w * p.tstride;
-    int32_t *H = p.H + (size_t)w * p.tstride;
+    const unsigned spanE = (unsigned)(R.y - R.x), spanM = (unsigned)(R.w - R.z);
+    Elem *tl = ((PREC == REWL_FP64) ? reinterpret_cast<Elem *>(p.lng)
+              : (PREC == REWL_F32X2) ? reinterpret_cast<Elem *>(p.lng2) : reinterpret_cast<Elem *>(p.lng1))
+             + (size_t)w * p.tstride;
+    int32_t *tH = p.H + (size_t)w * p.tstride;
     const double lnf = p.st->lnf;
-    const float lnf32 = trunc_to_float(lnf);   // exact for ln f = 2^-k, else within 2^-23
+    const float lnf32 = trunc_f(lnf);
     const uint32_t N = (uint32_t)p.N;
 
     int e = p.we[w], m = p.wm[w];
     int ci = (e - R.x) * wM + (m - R.z);
-    double lcur = lng[ci];
-    float base32 = trunc_to_float(lcur);
-    int q = 0;          // trials since base32 was taken
-    int hbase = H[ci];
-    long long pend = 0; // pending visits of the current bin
+    Val lbase = TB::load(tl, ci);
+    float base32 = TB::approx(lbase);
+    int lq = 0;          // ln f steps since lbase
+    int hq = 0;          // visits not yet in H
+    int hbase = tH[ci];
     unsigned long long t = p.wt[w];
     const unsigned long long tend = t + ntrials;
     int err = 0;
+
+    auto bitof = [&](int r, int c) -> uint32_t {
+        if (REG) return (uint32_t)(lat >> (r * L + c)) & 1u;
+        const int q = (WPR == 1) ? 0 : (c >> 5);
+        return (sm[(r * WPR + q) * nb] >> (c & 31)) & 1u;
+    };
 
     u32x4 x = philox10((uint32_t)(t >> 1), (uint32_t)(t >> 33), (uint32_t)w, TAG_TRIAL, p.key0, p.key1);
     while (t < tend) {
@@ -231,57 +240,69 @@ __global__ void __launch_bounds__(128) k_sweep_fp64(Params p, unsigned long long
         const int j = (int)site - i * L;
         const int iu = i == 0 ? L - 1 : i - 1, id = i == L - 1 ? 0 : i + 1;
         const int jl = j == 0 ? L - 1 : j - 1, jr = j == L - 1 ? 0 : j + 1;
-        const uint32_t s = sbit<WPR>(sm, nb, i, j);
-        const int nup = (int)(sbit<WPR>(sm, nb, iu, j) + sbit<WPR>(sm, nb, id, j)
-                            + sbit<WPR>(sm, nb, i, jl) + sbit<WPR>(sm, nb, i, jr));
-        const int en = e + (s ? nup - 2 : 2 - nup);
-        const int mn = m + (s ? -1 : 1);
-        if (en >= R.x && en <= R.y && mn >= R.z && mn <= R.w) {
+        const uint32_t sp = bitof(i, j);
+        const int nup = (int)(bitof(iu, j) + bitof(id, j) + bitof(i, jl) + bitof(i, jr));
+        const int en = e + (sp ? nup - 2 : 2 - nup);
+        const int mn = m + (sp ? -1 : 1);
+        if ((unsigned)(en - R.x) <= spanE && (unsigned)(mn - R.z) <= spanM) {
             const int ni = (en - R.x) * wM + (mn - R.z);
-            const double lnew = lng[ni];
-            const float b32 = trunc_to_float(lnew);
-            const float c32 = __fmaf_rn((float)q, lnf32, base32);
-            const float d32 = c32 - b32;
-            const float M = (fabsf(c32) + fabsf(b32) + fabsf(base32) + fabsf(lnu)) * 0x1p-20f + 0x1p-20f;
+            const Val tn = TB::load(tl, ni);
+            const float nb32 = TB::approx(tn);
             bool acc;
-            if (lnu < d32 - M) {
-                acc = true;
-            } else if (lnu > d32 + M) {
-                acc = false;
+            if constexpr (PREC == REWL_F32) {
+                acc = lnu < TB::add(lbase, lq, lnf, lnf32) - tn;
             } else {
-                const double delta = lcur - lnew;
-                acc = delta >= 0.0 || log(unit_open(xu)) < delta;
+                const float c32 = __fmaf_rn((float)lq, lnf32, base32);
+                const float d32 = c32 - nb32;
+                const float M = (fabsf(c32) + fabsf(nb32) + fabsf(base32) + fabsf(lnu)) * 0x1p-20f + 0x1p-20f;
+                if (lnu < d32 - M) {
+                    acc = true;
+                } else if (lnu > d32 + M) {
+                    acc = false;
+                } else {
+                    const double delta = fma((double)lq, lnf, TB::exact(lbase)) - TB::exact(tn);
+                    acc = delta >= 0.0 || log(unit_open_d(xu)) < delta;
+                }
             }
             if (acc) {
-                sm[(i * WPR + ((WPR == 1) ? 0 : (j >> 5))) * nb] ^= 1u << (j & 31);
-                if (pend) {
-                    const long long hv = (long long)(hbase < 0 ? 0 : hbase) + pend;
+                if (REG) lat ^= 1ull << (i * L + j);
+                else sm[(i * WPR + ((WPR == 1) ? 0 : (j >> 5))) * nb] ^= 1u << (j & 31);
+                if (hq) {
+                    const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
                     if (hv > 0x7FFFFFFFll) err = 1;
-                    lng[ci] = lcur;
-                    H[ci] = (int32_t)hv;
+                    tl[ci] = TB::add(lbase, lq, lnf, lnf32);
+                    tH[ci] = (int32_t)hv;
                 }
-                ci = ni; lcur = lnew; hbase = H[ni]; pend = 0;
-                base32 = b32; q = 0;
+                ci = ni; lbase = tn; base32 = nb32; lq = 0; hq = 0; hbase = tH[ni];
                 e = en; m = mn;
             }
         }
-        lcur += lnf;
-        ++pend;
-        if (++q == (1 << 22)) { base32 = trunc_to_float(lcur); q = 0; }
+        ++lq;
+        ++hq;
+        if (lq == (1 << 22)) {              // keep the float screen's counts exact
+            lbase = TB::add(lbase, lq, lnf, lnf32);
+            base32 = TB::approx(lbase);
+            lq = 0;
+        }
         ++t;
         if (!(t & 1ull))
             x = philox10((uint32_t)(t >> 1), (uint32_t)(t >> 33), (uint32_t)w, TAG_TRIAL, p.key0, p.key1);
     }
-    if (pend) {
-        const long long hv = (long long)(hbase < 0 ? 0 : hbase) + pend;
+    if (hq) {
+        const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
         if (hv > 0x7FFFFFFFll) err = 1;
-        lng[ci] = lcur;
-        H[ci] = (int32_t)hv;
+        tl[ci] = TB::add(lbase, lq, lnf, lnf32);
+        tH[ci] = (int32_t)hv;
     }
     p.we[w] = e;
     p.wm[w] = m;
     p.wt[w] = t;
-    for (int k = 0; k < nwords; ++k) p.spins[(size_t)k * p.nwalk + w] = sm[k * nb];
+    if (REG) {
+        for (int r = 0; r < L; ++r)
+            p.spins[(size_t)r * p.nwalk + w] = (uint32_t)(lat >> (r * L)) & (uint32_t)((1ull << L) - 1);
+    } else {
+        for (int k = 0; k < nwords; ++k) p.spins[(size_t)k * p.nwalk + w] = sm[k * nb];
+    }
     if (err) atomicOr(&p.st->error, ERR_OVERFLOW);
 }
 
@@ -298,16 +319,24 @@ cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int wpb, cudaStream_
     }
     if (wpb <= 0) wpb = 32;
     const int blocks = (p.nwalk + wpb - 1) / wpb;
-    const size_t smem = (size_t)p.nwords * wpb * sizeof(uint32_t);
-    if (p.precision != REWL_FP64) return cudaErrorNotSupported;
-    if (p.wpr == 1) {
-        k_sweep_fp64<1><<<blocks, wpb, smem, s>>>(p, (unsigned long long)ntrials);
-    } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_sweep_fp64<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_sweep_fp64<2><<<blocks, wpb, smem, s>>>(p, (unsigned long long)ntrials);
-    }
-    return cudaGetLastError();
+    const bool reg = p.N <= 64 && p.wpr == 1;
+    const size_t smem = reg ? 0 : (size_t)p.nwords * wpb * sizeof(uint32_t);
+    auto go = [&](auto kern) -> cudaError_t {
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<blocks, wpb, smem, s>>>(p, (unsigned long long)ntrials);
+        return cudaGetLastError();
+    };
+#define REWL_THREAD_P(P_)                                              \
+    if (reg) return go(k_sweep_thread<1, P_, true>);                   \
+    if (p.wpr == 1) return go(k_sweep_thread<1, P_, false>);           \
+    return go(k_sweep_thread<2, P_, false>);
+    if (p.precision == REWL_FP64) { REWL_THREAD_P(REWL_FP64) }
+    if (p.precision == REWL_F32X2) { REWL_THREAD_P(REWL_F32X2) }
+    REWL_THREAD_P(REWL_F32)
+#undef REWL_THREAD_P
 }
 
 // ----------------------------------------------------------- exchange ----

@@ -98,7 +98,7 @@ def test_host_init_spins(P):
 SAMPLERS = [0, 1]   # warp (tree speculation), thread
 
 
-@pytest.mark.parametrize("sampler,lanes,prec", [(0, 32, 0), (0, 16, 1), (0, 8, 0), (0, 32, 1), (1, 0, 0)])
+@pytest.mark.parametrize("sampler,lanes,prec", [(0, 32, 0), (0, 16, 1), (0, 8, 0), (0, 32, 1), (1, 0, 0), (1, 0, 1)])
 @pytest.mark.parametrize("L", [4, 5, 6, 8, 24, 33, 48, 64])
 def test_sweep_bit_exact_single_window(P, L, sampler, lanes, prec):
     """Sec. 2 trial/update rule, one window over the full (E, M) range; both
@@ -111,7 +111,7 @@ def test_sweep_bit_exact_single_window(P, L, sampler, lanes, prec):
         _compare(o, g)
 
 
-@pytest.mark.parametrize("sampler,prec", [(0, 0), (0, 1), (1, 0)])
+@pytest.mark.parametrize("sampler,prec", [(0, 0), (0, 1), (1, 0), (1, 1)])
 def test_cycles_bit_exact_L8_3x3(P, sampler, prec):
     """The 2D REWL workload at L = 8 (3 x 3 windows at 75% overlap, 4 walkers
     per window, exchange every 10^4 trials): whole cycles of sampling,
@@ -128,7 +128,7 @@ def test_cycles_bit_exact_L8_3x3(P, sampler, prec):
 
 
 @pytest.mark.parametrize("sampler,wpb,lanes,prec", [(0, 3, 32, 0), (0, 8, 32, 1), (0, 3, 8, 1), (0, 2, 16, 0),
-                                                     (1, 8, 0, 0)])
+                                                     (1, 8, 0, 0), (1, 8, 0, 1)])
 def test_cycles_with_check_interval_and_walkers_per_block(P, sampler, wpb, lanes, prec):
     """check_every > 1 (graph of several cycles) and a block size that leaves
     a ragged last block."""
@@ -218,14 +218,15 @@ def test_flatness_check_parity(P):
         _compare(o, g)
 
 
-def test_full_size_L32_batched_cycles(P):
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_full_size_L32_batched_cycles(P, sampler):
     """The batched workload at full size (L = 32, 16 x 4 windows, 32 walkers
     per window = 2048 walkers, exchange every 10^4 trials) in the launch
     configuration the benchmark times: two full cycles bit-identical."""
     from paper_1508_02748_gb300.workloads import REWL_L32 as w
     o, g = _pair(P, L=w.L, n_win_E=w.n_win_E, n_win_M=w.n_win_M, walkers_per_window=w.walkers_per_window,
                  exchange_interval=w.exchange_interval, check_every=w.check_every, seed=w.seed(0),
-                 drive_budget=10**8, precision=1)
+                 drive_budget=10**8, precision=1, sampler=sampler)
     o.run_cycles(2)
     g.run_cycles(2)
     so, spo = o.walkers()

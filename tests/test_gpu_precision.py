@@ -22,12 +22,13 @@ def P():
     return P
 
 
+@pytest.mark.parametrize("sampler", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "f32x2", "f32"])
-def test_lnf_increments_below_half_ulp(P, prec):
+def test_lnf_increments_below_half_ulp(P, prec, sampler):
     code = {"fp64": P.FP64, "f32x2": P.F32X2, "f32": P.F32}[prec]
     lnf = 2.0 ** -20                       # half an ulp of 40.0 in float is 2^-19
     run = P.REWL(P.Config(L=8, n_win_E=3, n_win_M=3, walkers_per_window=4, precision=code,
-                          lnf_init=lnf, seed=17))
+                          lnf_init=lnf, seed=17, sampler=sampler))
     lng, H = run.tables()
     lng[:] = 40.0
     H[:] = 0
