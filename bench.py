@@ -48,6 +48,23 @@ METRIC = "WL spin-flip trials/s & time-to-ln f=1e-6 at fixed ln g error, batched
 # periodic neighbours (~25), bin move, window test and table index (~12),
 # the screened acceptance (~10) and the bookkeeping of ln g / H (~8).
 OPS_PER_TRIAL = 120
+
+# DRAM bytes (read + write) per launch of the sampling kernel from one ncu
+# capture (profiles/k_sweep_tree_rewl_L8_3x3_w4.md), keyed by workload, kernel
+# and table format, valid only for the kernel sources they were taken on
+# (hash of the files below); any other case reports null.
+TRAFFIC_SOURCES = ("paper_1508_02748_gb300/csrc/rewl_sweep_tree.cu", "paper_1508_02748_gb300/csrc/rewl_tab.cuh",
+                   "paper_1508_02748_gb300/csrc/rewl_internal.cuh")
+TRAFFIC = {("rewl_L8_3x3_w4", "k_sweep_tree", "fp64", "7601443cd8495dcd"): 874496 + 0}
+
+
+def sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 ALU_LANES_PER_SM = 128          # 32-bit lanes per SM (4 partitions x 32)
 FALLBACK_SMS = 152
 
@@ -65,12 +82,19 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tiling")
     ap.add_argument("--lnf-final", type=float, default=None, help="override the workload's final ln f")
+    ap.add_argument("--walkers-per-window", type=int, default=None,
+                    help="override the workload's walkers per window (small cases for profiler captures)")
     ap.add_argument("--max-seconds", type=float, default=300.0,
                     help="--time-to: stop (and report the iteration reached) after this wall time")
     ap.add_argument("--precision", default=None, choices=["fp64", "f32x2", "f32"],
                     help="ln g tables (default: the workload's: fp64)")
     ap.add_argument("--sampler", default="auto", choices=["auto", "warp", "thread"],
                     help="auto: the autotuner picks the sampler too (with --no-autotune: warp)")
+    ap.add_argument("--replicate", type=int, default=0,
+                    help="seed replicate of the run (seed 20150811 + 1000 workload id + replicate + rank)")
+    ap.add_argument("--form", default="batched", choices=["batched", "plain"],
+                    help="plain: each walker's trials as a launch of their own (one thread, 4 streams), "
+                         "exchange and check launched from the host, no graph; same trajectory")
     ap.add_argument("--time-to", action="store_true",
                     help="run the workload to its final ln f and report the wall time and ln g error")
     return ap.parse_args()
@@ -271,9 +295,14 @@ def run_gpu(args, w):
     smp = {"auto": P.SAMPLER_WARP, "warp": P.SAMPLER_WARP, "thread": P.SAMPLER_THREAD}[args.sampler]
     if args.lnf_final is not None:
         w = w.with_(lnf_final=args.lnf_final)
-    cfg = P.Config.from_workload(w, replicate=replica_seed_index(rank), drive_budget=10**8, precision=prec,
+    if args.walkers_per_window is not None:
+        w = w.with_(walkers_per_window=args.walkers_per_window,
+                    name=f"{w.name.rsplit('_w', 1)[0]}_w{args.walkers_per_window}")
+    cfg = P.Config.from_workload(w, replicate=args.replicate + replica_seed_index(rank), drive_budget=10**8,
+                                 precision=prec,
                                  sampler=smp)
-    if not args.no_autotune:
+    plain = args.form == "plain"
+    if not args.no_autotune and not plain:
         from paper_1508_02748_gb300.autotune import autotune
         allowed = (P.SAMPLER_WARP, P.SAMPLER_THREAD) if args.sampler == "auto" else (smp,)
         cfg = autotune(cfg, device=str(dev), samplers=allowed)
@@ -284,9 +313,10 @@ def run_gpu(args, w):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     nwalk_active = run.status()["n_walkers"]
     trials_per_step = w.exchange_interval * nwalk_active
+    sample_part = P.PART_SAMPLE_PLAIN if plain else P.PART_SAMPLE
     with torch.cuda.stream(s):
         for _ in range(args.warmup):
-            run.enqueue_cycle()
+            run.enqueue_cycle(sample_part | P.PART_REST)
     s.synchronize()
 
     K = args.steps
@@ -301,12 +331,12 @@ def run_gpu(args, w):
         for k in range(K):
             flush.zero_()                                # L2 flush, outside the step's events
             ev[k][0].record(s)
-            run.enqueue_cycle(P.PART_SAMPLE)
+            run.enqueue_cycle(sample_part)
             ev[k][1].record(s)
             run.enqueue_cycle(P.PART_REST)
             ev[k][2].record(s)
             check = ((args.warmup + k + 1) % w.check_every) == 0
-            launches += 3 + (2 if check else 0)
+            launches += (nwalk_active if plain else 1) + 2 + (2 if check else 0)
     s.synchronize()
     torch.cuda.synchronize()
     barrier()
@@ -323,9 +353,12 @@ def run_gpu(args, w):
     peak_ops = sm_count * ALU_LANES_PER_SM * mhz * 1e6
     sweep_s = statistics.mean(sweep_ms) / 1e3
     achieved = OPS_PER_TRIAL * trials_per_step / sweep_s
+    kname = "k_sweep_tree" if cfg.sampler == P.SAMPLER_WARP and not plain else "k_sweep_thread"
+    traffic = TRAFFIC.get((w.name, kname, args.precision, sources_hash())) if not plain else None
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops, "traffic": None,
-            "kernel": "k_sweep_tree" if cfg.sampler == P.SAMPLER_WARP else "k_sweep_thread",
+            "frac": achieved / peak_ops, "traffic": traffic,
+            "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "kernel": kname + (" (one launch per walker, 4 streams)" if plain else ""),
             "kernel_ms_mean": sweep_s * 1e3,
             "kernel_share_of_step": sum(sweep_ms) / total_ms,
             "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x median SM clock {mhz:.0f} MHz (derived)"}
@@ -341,7 +374,7 @@ def run_gpu(args, w):
         t0 = time.perf_counter()
         run2 = P.REWL(cfg, init_spins=pinned, device=str(dev), stream=s)
         for _ in range(K):
-            run2.run_cycles(1)
+            (run2.run_cycles_plain if plain else run2.run_cycles)(1)
         J = run2.lng()
         t1 = time.perf_counter()
         out[:] = J.ravel()
@@ -361,7 +394,8 @@ def run_gpu(args, w):
                 "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
                 "data": "synthetic",
                 "config": dict(_config_dict(w, "flushed between steps (256 MiB write, outside the step events)",
-                                            args.precision, _sampler_name(cfg.sampler)),
+                                            args.precision, "thread" if plain else _sampler_name(cfg.sampler)),
+                               form=args.form,
                                tiling={"sampler": cfg.sampler, "lanes_per_walker": cfg.lanes_per_walker,
                                        "walkers_per_block": cfg.walkers_per_block}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
@@ -388,8 +422,9 @@ def run_time_to(args, w, cfg, dev):
     st = run.status()
     chunk = 64 * w.check_every
     capped = False
+    step = run.run_cycles_plain if args.form == "plain" else run.run_cycles
     while not st["done"]:
-        st = run.run_cycles(chunk)
+        st = step(chunk)
         if time.perf_counter() - t0 > args.max_seconds:
             capped = True
             break
@@ -405,8 +440,11 @@ def run_time_to(args, w, cfg, dev):
         eps = float(np.mean(np.abs(mE[ok] - ex[ok]) / ex[ok]))
     line = {"metric": "time-to-ln f<=%g" % w.lnf_final, "value": elapsed, "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
-            "data": "synthetic", "config": _config_dict(w, "n/a", args.precision, _sampler_name(cfg.sampler)),
-            "capped": capped, "max_seconds": args.max_seconds,
+            "data": "synthetic",
+            "config": dict(_config_dict(w, "n/a", args.precision,
+                                        "thread" if args.form == "plain" else _sampler_name(cfg.sampler)),
+                           form=args.form),
+            "seed": cfg.seed, "capped": capped, "max_seconds": args.max_seconds,
             "iterations": st["iteration"], "cycles": st["cycles"], "trials_per_walker": st["trials"],
             "lnf_final": st["lnf"], "mean_eps_E_marginal_vs_exact": eps,
             "exchange_acceptance": st["exch_accepts"] / max(1, st["exch_attempts"])}

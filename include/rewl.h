@@ -139,6 +139,9 @@ int rewl_run_iteration(rewl_t *h, uint64_t max_cycles, rewl_status *status);
 /* Parts of one cycle for rewl_enqueue_cycle. */
 #define REWL_PART_SAMPLE 1      /* the exchange_interval trials of every walker */
 #define REWL_PART_REST 2        /* exchange sweep, flatness check (every check_every cycles), counters */
+#define REWL_PART_SAMPLE_PLAIN 4 /* the same trials in the plain form (see rewl_run_cycles_plain);
+                                    not together with REWL_PART_SAMPLE */
+#define REWL_PLAIN_STREAMS 4    /* streams the plain form spreads its launches over */
 
 /* Queues one cycle, or the given parts of it in order SAMPLE then REST, on
  * the run's stream and returns without waiting: the asynchronous form of
@@ -147,6 +150,18 @@ int rewl_run_iteration(rewl_t *h, uint64_t max_cycles, rewl_status *status);
  * Errors are those of queueing (REWL_E_INVALID, REWL_E_CUDA); device errors
  * surface at the next synchronous call. */
 int rewl_enqueue_cycle(rewl_t *h, int parts);
+
+/* The same cycles as rewl_run_cycles, with the same result bit for bit (the
+ * chain of every walker does not depend on how it is scheduled), executed in
+ * the plain unbatched form the batched sampler is measured against: each
+ * walker's exchange_interval trials are a launch of their own (one thread of
+ * the one-thread-per-walker kernel, whatever sampler the run was created
+ * with), spread round-robin over REWL_PLAIN_STREAMS library-owned streams
+ * forked from and joined back into the run's stream; the exchange, flatness
+ * check and advance follow as separate launches; no CUDA graph.  The walkers
+ * of one exchange interval are independent (Sec. 2), so the order of their
+ * launches is free.  status may be NULL.  Errors as rewl_run_cycles. */
+int rewl_run_cycles_plain(rewl_t *h, uint64_t n_cycles, rewl_status *status);
 
 /* Single steps (also used inside the cycle): n trials per walker; one
  * exchange sweep of the current phase; one flatness check with advance. */

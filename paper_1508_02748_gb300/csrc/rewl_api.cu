@@ -31,6 +31,12 @@ struct rewl_s {
     bool graph_ok;
     int first_active;                // a walker of a non-empty window (-1 if none)
     double *jk_mean, *jk_err;        // jackknife results (device)
+    std::vector<int> live;           // walkers of non-empty windows, in walker order
+    // plain form: streams the per-walker launches are spread over, and one
+    // event per stream plus one on the run's stream to fork and join them
+    cudaStream_t plain_s[REWL_PLAIN_STREAMS];
+    cudaEvent_t plain_ev[REWL_PLAIN_STREAMS + 1];
+    bool plain_ok;
 };
 
 namespace {
@@ -420,6 +426,8 @@ int create_impl(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_
     h->first_active = -1;
     for (int win = 0; win < d.nwin && h->first_active < 0; ++win)
         if (active[win]) h->first_active = win * d.W;
+    for (int w = 0; w < d.nwalk; ++w)
+        if (active[w / d.W]) h->live.push_back(w);
 
     auto bail = [&](int code) { rewl_destroy(h); return code; };
     DevState ds;
@@ -605,10 +613,42 @@ extern "C" int rewl_run_cycles(rewl_t *h, uint64_t n_cycles, rewl_status *status
     return REWL_OK;
 }
 
+namespace {
+
+// The plain form of a cycle's sampling: one single-thread launch per walker,
+// round-robin over REWL_PLAIN_STREAMS streams forked from and joined back
+// into the run's stream.
+int queue_sample_plain(rewl_t *h)
+{
+    if (!h->plain_ok) {
+        for (int i = 0; i < REWL_PLAIN_STREAMS; ++i)
+            CK(h, cudaStreamCreateWithFlags(&h->plain_s[i], cudaStreamNonBlocking));
+        for (int i = 0; i <= REWL_PLAIN_STREAMS; ++i)
+            CK(h, cudaEventCreateWithFlags(&h->plain_ev[i], cudaEventDisableTiming));
+        h->plain_ok = true;
+    }
+    CK(h, cudaEventRecord(h->plain_ev[REWL_PLAIN_STREAMS], h->stream));
+    for (int i = 0; i < REWL_PLAIN_STREAMS; ++i) CK(h, cudaStreamWaitEvent(h->plain_s[i], h->plain_ev[REWL_PLAIN_STREAMS], 0));
+    for (size_t k = 0; k < h->live.size(); ++k)
+        CK(h, launch_sweep_walker(h->p, h->live[k], h->cfg.exchange_interval, h->plain_s[k % REWL_PLAIN_STREAMS]));
+    for (int i = 0; i < REWL_PLAIN_STREAMS; ++i) {
+        CK(h, cudaEventRecord(h->plain_ev[i], h->plain_s[i]));
+        CK(h, cudaStreamWaitEvent(h->stream, h->plain_ev[i], 0));
+    }
+    return REWL_OK;
+}
+
+}  // namespace
+
 extern "C" int rewl_enqueue_cycle(rewl_t *h, int parts)
 {
-    if (!h || parts < 1 || parts > 3) return fail(h, REWL_E_INVALID, "bad parts %d", parts);
+    if (!h || parts < 1 || parts > 7 || ((parts & REWL_PART_SAMPLE) && (parts & REWL_PART_SAMPLE_PLAIN)))
+        return fail(h, REWL_E_INVALID, "bad parts %d", parts);
     if (parts & REWL_PART_SAMPLE) CK(h, launch_sweep(h->p, h->cfg.exchange_interval, h->wpb, h->stream));
+    if (parts & REWL_PART_SAMPLE_PLAIN) {
+        const int rc = queue_sample_plain(h);
+        if (rc) return rc;
+    }
     if (parts & REWL_PART_REST) {
         const bool check = (h->host_cycle + 1) % (unsigned long long)h->cfg.check_every == 0;
         CK(h, launch_exchange(h->p, h->max_pairs, h->stream));
@@ -617,6 +657,20 @@ extern "C" int rewl_enqueue_cycle(rewl_t *h, int parts)
         if (check) CK(h, launch_reset(h->p, h->stream));
         h->host_cycle += 1;
     }
+    return REWL_OK;
+}
+
+extern "C" int rewl_run_cycles_plain(rewl_t *h, uint64_t n_cycles, rewl_status *status)
+{
+    if (!h) return REWL_E_INVALID;
+    for (uint64_t c = 0; c < n_cycles; ++c) {
+        const int rc = rewl_enqueue_cycle(h, REWL_PART_SAMPLE_PLAIN | REWL_PART_REST);
+        if (rc) return rc;
+    }
+    DevState ds;
+    int rc = read_state(h, &ds);
+    if (rc) return rc;
+    fill_status(h, ds, status);
     return REWL_OK;
 }
 
@@ -866,6 +920,10 @@ extern "C" int rewl_destroy(rewl_t *h)
 {
     if (!h) return REWL_OK;
     if (h->graph_ok) cudaGraphExecDestroy(h->graph);
+    if (h->plain_ok) {
+        for (int i = 0; i < REWL_PLAIN_STREAMS; ++i) cudaStreamDestroy(h->plain_s[i]);
+        for (int i = 0; i <= REWL_PLAIN_STREAMS; ++i) cudaEventDestroy(h->plain_ev[i]);
+    }
     delete h;
     return REWL_OK;
 }

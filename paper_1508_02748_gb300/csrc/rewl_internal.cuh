@@ -79,6 +79,7 @@ struct Params {
     uint64_t drive_budget;
 
     int join_exclude; // merge: walker index within each window left out (-1: none)
+    int walker0;      // thread sampler: walker of thread 0 of block 0 (0 for a whole sweep)
 
     const int4 *rect;       // per window: e0, e1, m0, m1
     const int32_t *active;  // per window: 1 if it can hold a configuration
@@ -118,6 +119,8 @@ struct JoinScratch {
 cudaError_t launch_init(const Params &p, const uint8_t *d_init_bytes, cudaStream_t s);
 cudaError_t launch_drive(const Params &p, int32_t *d_fail, cudaStream_t s);
 cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int walkers_per_block, cudaStream_t s);
+// Sweep of walker w alone: one thread of the one-thread-per-walker kernel.
+cudaError_t launch_sweep_walker(const Params &p, int w, uint64_t ntrials, cudaStream_t s);
 cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int warps, bool smt, cudaStream_t s);
 size_t tree_smem_per_warp(const Params &p, bool smt);
 cudaError_t launch_exchange(const Params &p, int max_pairs, cudaStream_t s);

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128) k_sweep_thread(Params p, unsigned long lo
     using Val = typename TB::Val;
     extern __shared__ uint32_t sm_all[];
     const int nb = blockDim.x, tid = threadIdx.x;
-    const int w = blockIdx.x * nb + tid;
+    const int w = p.walker0 + blockIdx.x * nb + tid;
     if (w >= p.nwalk) return;
     if (!p.active[w / p.W] || p.st->done) return;
     uint32_t *sm = sm_all + tid;
@@ -306,19 +306,11 @@ __global__ void __launch_bounds__(128) k_sweep_thread(Params p, unsigned long lo
     if (err) atomicOr(&p.st->error, ERR_OVERFLOW);
 }
 
-cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int wpb, cudaStream_t s)
+namespace {
+
+// blocks x wpb threads of k_sweep_thread, walkers p.walker0 onwards.
+cudaError_t launch_thread(const Params &p, int blocks, int wpb, uint64_t ntrials, cudaStream_t s)
 {
-    if (p.sampler == REWL_SAMPLER_WARP) {
-        while (ntrials > 0) {
-            const uint64_t n = ntrials > (1ull << 30) ? (1ull << 30) : ntrials;
-            const cudaError_t e = launch_sweep_tree(p, n, p.group, wpb, p.smt != 0, s);
-            if (e != cudaSuccess) return e;
-            ntrials -= n;
-        }
-        return cudaSuccess;
-    }
-    if (wpb <= 0) wpb = 32;
-    const int blocks = (p.nwalk + wpb - 1) / wpb;
     const bool reg = p.N <= 64 && p.wpr == 1;
     const size_t smem = reg ? 0 : (size_t)p.nwords * wpb * sizeof(uint32_t);
     auto go = [&](auto kern) -> cudaError_t {
@@ -337,6 +329,30 @@ cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int wpb, cudaStream_
     if (p.precision == REWL_F32X2) { REWL_THREAD_P(REWL_F32X2) }
     REWL_THREAD_P(REWL_F32)
 #undef REWL_THREAD_P
+}
+
+}  // namespace
+
+cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int wpb, cudaStream_t s)
+{
+    if (p.sampler == REWL_SAMPLER_WARP) {
+        while (ntrials > 0) {
+            const uint64_t n = ntrials > (1ull << 30) ? (1ull << 30) : ntrials;
+            const cudaError_t e = launch_sweep_tree(p, n, p.group, wpb, p.smt != 0, s);
+            if (e != cudaSuccess) return e;
+            ntrials -= n;
+        }
+        return cudaSuccess;
+    }
+    if (wpb <= 0) wpb = 32;
+    return launch_thread(p, (p.nwalk + wpb - 1) / wpb, wpb, ntrials, s);
+}
+
+cudaError_t launch_sweep_walker(const Params &p, int w, uint64_t ntrials, cudaStream_t s)
+{
+    Params q = p;
+    q.walker0 = w;
+    return launch_thread(q, 1, 1, ntrials, s);
 }
 
 // ----------------------------------------------------------- exchange ----

@@ -21,7 +21,7 @@ REWL_OK = 0
 ERRORS = {-1: "INVALID", -2: "CUDA", -3: "TIMEOUT", -4: "UNREACHABLE", -5: "OVERFLOW",
           -6: "BUDGET", -7: "JOIN", -8: "CAPACITY"}
 FP64, F32X2, F32 = 0, 1, 2
-PART_SAMPLE, PART_REST = 1, 2
+PART_SAMPLE, PART_REST, PART_SAMPLE_PLAIN = 1, 2, 4
 SAMPLER_WARP, SAMPLER_THREAD = 0, 1
 LNG_JOINED, LNG_MARGINAL_E = 0, 1
 
@@ -59,6 +59,7 @@ SIGNATURES = {
     "rewl_workspace_size": (ctypes.c_int, [ctypes.POINTER(rewl_config), ctypes.POINTER(ctypes.c_size_t)]),
     "rewl_create": (ctypes.c_int, [ctypes.POINTER(rewl_config), _P, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "rewl_run_cycles": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(rewl_status)]),
+    "rewl_run_cycles_plain": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(rewl_status)]),
     "rewl_run_iteration": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(rewl_status)]),
     "rewl_enqueue_cycle": (ctypes.c_int, [_P, ctypes.c_int]),
     "rewl_sweep": (ctypes.c_int, [_P, ctypes.c_uint64]),
@@ -193,6 +194,12 @@ class REWL:
     def run_cycles(self, n: int) -> dict:
         s = rewl_status()
         _check(load_library().rewl_run_cycles(self._h, n, ctypes.byref(s)), self._h)
+        return _status_dict(s)
+
+    def run_cycles_plain(self, n: int) -> dict:
+        """The same cycles in the plain form: one launch per walker, no graph."""
+        s = rewl_status()
+        _check(load_library().rewl_run_cycles_plain(self._h, n, ctypes.byref(s)), self._h)
         return _status_dict(s)
 
     def run_iteration(self, max_cycles: int) -> tuple[bool, dict]:

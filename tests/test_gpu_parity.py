@@ -127,6 +127,33 @@ def test_cycles_bit_exact_L8_3x3(P, sampler, prec):
     assert o.info()["exch_accept"] > 0
 
 
+@pytest.mark.parametrize("sampler,prec", [(0, 0), (1, 1)])
+def test_plain_form_bit_exact_L8_3x3(P, sampler, prec):
+    """The plain form (one launch per walker over several streams, host-driven
+    exchange and check, no graph) is the same chain: bit-identical to the
+    oracle, also when interleaved with batched cycles and with check_every > 1
+    splitting check blocks between the two forms."""
+    o, g = _pair(P, L=8, n_win_E=3, n_win_M=3, walkers_per_window=4, exchange_interval=10000,
+                 check_every=3, seed=20152813, sampler=sampler, precision=prec)
+    for chunk, plain in ((1, True), (2, False), (7, True), (40, False), (61, True), (150, False), (100, True)):
+        o.run_cycles(chunk)
+        (g.run_cycles_plain if plain else g.run_cycles)(chunk)
+        _compare(o, g)
+    assert o.info()["iter"] >= 2      # two iteration advances (the second one in plain cycles)
+
+
+def test_plain_form_skips_empty_windows(P):
+    """L = 8, 6 x 6 windows at 50% overlap (four windows can hold no
+    configuration and get no walkers): the plain form launches only walkers of
+    non-empty windows and matches the oracle."""
+    o, g = _pair(P, L=8, n_win_E=6, n_win_M=6, overlap_E=0.5, overlap_M=0.5, walkers_per_window=2,
+                 exchange_interval=2000, seed=4242)
+    for chunk in (1, 5, 12):
+        o.run_cycles(chunk)
+        g.run_cycles_plain(chunk)
+        _compare(o, g)
+
+
 @pytest.mark.parametrize("sampler,wpb,lanes,prec", [(0, 3, 32, 0), (0, 8, 32, 1), (0, 3, 8, 1), (0, 2, 16, 0),
                                                      (1, 8, 0, 0), (1, 8, 0, 1)])
 def test_cycles_with_check_interval_and_walkers_per_block(P, sampler, wpb, lanes, prec):
