@@ -76,6 +76,7 @@ def lib():
             L.orc_join_excl.argtypes = [P, i32, P, P, P]
             L.orc_join_excl.restype = i32
             L.orc_marginal_e.argtypes = [i32, P, P]
+            L.orc_rel_diff.argtypes = [ctypes.c_size_t, P, P, P]
             L.orc_bin_possible.argtypes = [i32, i32, i32]
             L.orc_bin_possible.restype = i32
             L.orc_enum_gEM.argtypes = [i32, P]
@@ -283,4 +284,16 @@ def marginal_e(lng_joint: np.ndarray) -> np.ndarray:
     a = np.ascontiguousarray(lng_joint, dtype=np.float64)
     out = np.zeros(B, dtype=np.float64)
     lib().orc_marginal_e(B - 1, _ptr(a), _ptr(out))
+    return out
+
+
+def relative_difference(lng_a: np.ndarray, lng_b: np.ndarray) -> np.ndarray:
+    """Eq. 5 per bin from two ln g tables of the same shape: |g_a - g_b| / gbar,
+    gbar = (g_a + g_b) / 2; 2 where one table is empty, NaN where both are."""
+    a = np.ascontiguousarray(lng_a, dtype=np.float64)
+    b = np.ascontiguousarray(lng_b, dtype=np.float64)
+    if a.shape != b.shape:
+        raise ValueError("tables differ in shape")
+    out = np.empty_like(a)
+    lib().orc_rel_diff(a.size, _ptr(a), _ptr(b), _ptr(out))
     return out

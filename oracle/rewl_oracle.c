@@ -25,6 +25,7 @@
  *   beta(E) = d ln g/dE, E_mat = argmin |beta_i - beta_j|, rescale,
  *   piecewise join                                                  ... Eq. 4
  *   E and M both split: match one dimension at a time               ... Sec. 2
+ *   relative difference of two g(E,M) tables                        ... Eq. 5
  *
  * Readings of points the paper leaves open (each one is listed in the design
  * notes of the repository):
@@ -742,4 +743,21 @@ void orc_marginal_e(int N, const double *joined, double *out)
 {
     int B = N + 1;
     for (int e = 0; e < B; ++e) out[e] = logsumexp(joined + (size_t)e * B, (size_t)B, 1);
+}
+
+/* Relative difference of two density-of-states tables, Eq. 5:
+ * |g_a - g_b| / gbar with gbar = (g_a + g_b) / 2, per bin, from ln g_a and
+ * ln g_b.  Numerator and denominator are both scaled by exp(-max(ln g_a,
+ * ln g_b)) so that the exponentials stay finite at any size; a bin empty in
+ * one table only gives 2, a bin empty in both NaN (no value). */
+void orc_rel_diff(size_t n, const double *lga, const double *lgb, double *out)
+{
+    for (size_t i = 0; i < n; ++i) {
+        const double a = lga[i], b = lgb[i];
+        if (a == -INFINITY && b == -INFINITY) { out[i] = NAN; continue; }
+        const double s = a > b ? a : b;
+        const double ga = exp(a - s), gb = exp(b - s);
+        const double gbar = (ga + gb) / 2.0;
+        out[i] = fabs(ga - gb) / gbar;
+    }
 }
