@@ -29,6 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, E_INVALID, E_UNREACHABLE, E_JOIN = 0, -1, -4, -7
+JOIN_MARGINAL, JOIN_PER_SLICE = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -75,6 +76,8 @@ def lib():
             L.orc_join.restype = i32
             L.orc_join_excl.argtypes = [P, i32, P, P, P]
             L.orc_join_excl.restype = i32
+            L.orc_join_rule.argtypes = [P, i32, i32, P, P, P]
+            L.orc_join_rule.restype = i32
             L.orc_marginal_e.argtypes = [i32, P, P]
             L.orc_rel_diff.argtypes = [ctypes.c_size_t, P, P, P]
             L.orc_bin_possible.argtypes = [i32, i32, i32]
@@ -225,14 +228,17 @@ class OracleREWL:
         H = np.ascontiguousarray(H, dtype=np.int32)
         lib().orc_set_tables(self._h, _ptr(lng), _ptr(H))
 
-    def join(self):
-        """Merged, joined and normalised ln g(e, m) plus the matching points."""
+    def join(self, rule: int = JOIN_MARGINAL):
+        """Merged, joined and normalised ln g(e, m) plus the matching points;
+        rule JOIN_MARGINAL rescales each piece by one constant (the marginals'
+        difference at the matching point), JOIN_PER_SLICE each M slice (each E
+        slice in the join along M) by its own difference there."""
         B = self.N + 1
         c = self.cfg
         out = np.zeros((B, B), dtype=np.float64)
         em = np.zeros(max(1, c.n_win_M * max(1, c.n_win_E - 1)), dtype=np.int32)
         mm = np.zeros(max(1, c.n_win_M - 1), dtype=np.int32)
-        rc = lib().orc_join(self._h, _ptr(out), _ptr(em), _ptr(mm))
+        rc = lib().orc_join_rule(self._h, -1, rule, _ptr(out), _ptr(em), _ptr(mm))
         if rc:
             raise RuntimeError(f"oracle join failed: code {rc}")
         return out, em, mm

@@ -621,18 +621,31 @@ static int match_point(const double *Ga, const double *Gb, int lo, int hi, int f
  * order, -inf where no walker visited, normalised so sum g = 2^N.
  * ematch: nM x (nE-1) E matching points (-1 where unused);
  * mmatch: (nM-1) M matching points. */
-int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int32_t *mmatch);
+int orc_join_rule(const orc_rewl *s, int excl, int rule, double *out, int32_t *ematch, int32_t *mmatch);
 
 int orc_join(const orc_rewl *s, double *out, int32_t *ematch, int32_t *mmatch)
 {
-    return orc_join_excl(s, -1, out, ematch, mmatch);
+    return orc_join_rule(s, -1, 0, out, ematch, mmatch);
 }
 
 /* The join with walker `excl` of every window left out of the merge (-1:
  * none); excl >= 0 needs at least two walkers per window. */
 int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int32_t *mmatch)
 {
-    if (excl >= s->W || (excl >= 0 && s->W < 2)) return ORC_E_INVALID;
+    return orc_join_rule(s, excl, 0, out, ematch, mmatch);
+}
+
+/* Rescaling rule of a join step (Eq. 4 and the sentence before it: the
+ * surface is rescaled "at g(E_mat, M)").
+ *   rule 0: one constant per piece, the difference of the two pieces'
+ *           marginals (Eq. 3) at the matching point;
+ *   rule 1: one constant per slice: for every M of the piece, the
+ *           difference ln g_i(E_mat, M) - ln g_j(E_mat, M) where both pieces
+ *           have that bin, else the marginal difference of rule 0; joining
+ *           rows along M, the same per E at M_mat. */
+int orc_join_rule(const orc_rewl *s, int excl, int rule, double *out, int32_t *ematch, int32_t *mmatch)
+{
+    if (excl >= s->W || (excl >= 0 && s->W < 2) || rule < 0 || rule > 1) return ORC_E_INVALID;
     int N = s->N, B = N + 1, nE = s->nE, nM = s->nM;
     for (size_t i = 0; i < (size_t)B * B; ++i) out[i] = -INFINITY;
     double **piece = (double **)calloc(s->nwin, sizeof(double *));
@@ -647,6 +660,7 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
     /* rows[b]: full-width table B x B for row b (-inf outside). */
     double **rows = (double **)calloc(nM, sizeof(double *));
     double *Ga = (double *)malloc(sizeof(double) * B), *Gb = (double *)malloc(sizeof(double) * B);
+    double *sl = (double *)malloc(sizeof(double) * B), *sl_next = (double *)malloc(sizeof(double) * B);
     int *row_ok = (int *)calloc(nM, sizeof(int));
     for (int b = 0; b < nM && rc == ORC_OK; ++b) {
         int first = -1, last = -1;
@@ -660,6 +674,7 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
         for (size_t i = 0; i < (size_t)B * B; ++i) rows[b][i] = -INFINITY;
         row_ok[b] = 1;
         double shift = 0.0;      /* shift of the current piece */
+        for (int m = 0; m < B; ++m) sl[m] = 0.0;   /* rule 1: shift of each M slice */
         int from = s->e0[b * nE + first];
         for (int a = first; a <= last; ++a) {
             int A = b * nE + a;
@@ -678,6 +693,13 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
                 if (p < 0) { rc = ORC_E_JOIN; break; }
                 ematch[b * (nE - 1) + a] = p;
                 next_shift = shift + (Ga[p] - Gb[p]);
+                for (int m = 0; m < B; ++m) sl_next[m] = sl[m] + (Ga[p] - Gb[p]);
+                if (rule == 1)
+                    for (int m = s->m0[A]; m <= s->m1[A]; ++m) {
+                        double va = piece[A][(size_t)(p - s->e0[A]) * wM + (m - s->m0[A])];
+                        double vb = piece[Bw][(size_t)(p - s->e0[Bw]) * wM + (m - s->m0[Bw])];
+                        if (va != -INFINITY && vb != -INFINITY) sl_next[m] = sl[m] + (va - vb);
+                    }
                 to = p;
             } else {
                 to = s->e1[A] + 1;
@@ -685,9 +707,11 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
             for (int e = from; e < to; ++e)
                 for (int m = s->m0[A]; m <= s->m1[A]; ++m) {
                     double v = piece[A][(size_t)(e - s->e0[A]) * wM + (m - s->m0[A])];
-                    rows[b][(size_t)e * B + m] = v == -INFINITY ? v : v + shift;
+                    double c = rule == 1 ? sl[m] : shift;
+                    rows[b][(size_t)e * B + m] = v == -INFINITY ? v : v + c;
                 }
             shift = next_shift;
+            for (int m = 0; m < B; ++m) sl[m] = sl_next[m];
             from = to;
         }
     }
@@ -698,6 +722,7 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
         for (int b = first; b >= 0 && b <= last; ++b) if (!row_ok[b]) { rc = ORC_E_JOIN; break; }
         if (first < 0) rc = ORC_E_JOIN;
         double shift = 0.0;
+        for (int e = 0; e < B; ++e) sl[e] = 0.0;   /* rule 1: shift of each E slice */
         int from = rc == ORC_OK ? s->m0[first * nE] : 0;
         for (int b = first; rc == ORC_OK && b <= last; ++b) {
             int to;
@@ -712,6 +737,11 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
                 if (p < 0) { rc = ORC_E_JOIN; break; }
                 mmatch[b] = p;
                 next_shift = shift + (Ga[p] - Gb[p]);
+                for (int e = 0; e < B; ++e) {
+                    double va = rows[b][(size_t)e * B + p], vb = rows[b + 1][(size_t)e * B + p];
+                    double d = (rule == 1 && va != -INFINITY && vb != -INFINITY) ? va - vb : Ga[p] - Gb[p];
+                    sl_next[e] = sl[e] + d;
+                }
                 to = p;
             } else {
                 to = s->m1[b * nE] + 1;
@@ -719,9 +749,11 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
             for (int e = 0; e < B; ++e)
                 for (int m = from; m < to; ++m) {
                     double v = rows[b][(size_t)e * B + m];
-                    out[(size_t)e * B + m] = v == -INFINITY ? v : v + shift;
+                    double c = rule == 1 ? sl[e] : shift;
+                    out[(size_t)e * B + m] = v == -INFINITY ? v : v + c;
                 }
             shift = next_shift;
+            for (int e = 0; e < B; ++e) sl[e] = sl_next[e];
             from = to;
         }
     }
@@ -734,7 +766,7 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
     }
     for (int w = 0; w < s->nwin; ++w) free(piece[w]);
     for (int b = 0; b < nM; ++b) free(rows[b]);
-    free(piece); free(rows); free(Ga); free(Gb); free(row_ok);
+    free(piece); free(rows); free(Ga); free(Gb); free(sl); free(sl_next); free(row_ok);
     return rc;
 }
 

@@ -120,3 +120,89 @@ def test_paper_shape_L6_rewl_against_serial_wl_eq5():
         mM = mx + np.log(np.exp(Jre - mx).sum(axis=0))
     lbin = np.array([math.log(math.comb(N, m)) for m in range(N + 1)])
     assert np.abs(mM[1:N] - lbin[1:N]).max() < 0.1
+
+
+# ------------------------------------------- rescaling rule of a join step --
+
+def _exact_pieces(r, lg, distort, rng):
+    """Set every walker's table to the exact ln g of its window, plus a random
+    constant per walker and distort(window, e, m) for the window's bins."""
+    w = r.windows()
+    W = r.cfg.walkers_per_window
+    lng, H, toff = r.tables()
+    for k in range(toff.size - 1):
+        e0, e1, m0, m1, _ = w[k // W]
+        ee, mm = np.meshgrid(np.arange(e0, e1 + 1), np.arange(m0, m1 + 1), indexing="ij")
+        blk = lg[e0:e1 + 1, m0:m1 + 1]
+        seen = np.isfinite(blk)
+        val = blk + rng.normal() * 20 + distort(k // W, ee, mm)
+        lng[toff[k]:toff[k + 1]] = np.where(seen, val, 0.0).ravel()
+        H[toff[k]:toff[k + 1]] = np.where(seen, 1, -1).ravel()
+    r.set_tables(lng, H)
+
+
+def test_both_rescaling_rules_reconstruct_exact_pieces_L6():
+    """Pieces that differ from the exact table by a constant per walker are
+    joined back to the exact table by either rescaling rule, E and M split."""
+    L = 6
+    g = oracle.transfer_gEM(L)
+    lg = _lg(g)
+    occ = g > 0
+    for rule in (oracle.JOIN_MARGINAL, oracle.JOIN_PER_SLICE):
+        r = OracleREWL(OracleConfig(L=L, n_win_E=3, n_win_M=2, walkers_per_window=2, seed=21))
+        _exact_pieces(r, lg, lambda win, e, m: 0.0, np.random.default_rng(rule))
+        J, _, _ = r.join(rule)
+        assert np.array_equal(np.isfinite(J), occ)
+        assert np.abs(J[occ] - lg[occ]).max() < 1e-9
+
+
+def _spread(x):
+    return float(x.max() - x.min())
+
+
+def test_per_slice_rule_removes_slice_offsets_E_join_L6():
+    """Two E windows (M unrestricted); the upper one carries an offset that
+    depends on M alone.  Rescaling per M slice at E_mat (rule 1) puts every
+    slice that is occupied at E_mat back on the exact table (one common
+    constant, fixed by the normalisation); the single marginal constant
+    (rule 0) leaves the offsets in."""
+    L = 6
+    g = oracle.transfer_gEM(L)
+    lg = _lg(g)
+    occ = g > 0
+    delta = np.random.default_rng(5).uniform(-0.3, 0.3, size=L * L + 1)
+    out = {}
+    for rule in (oracle.JOIN_MARGINAL, oracle.JOIN_PER_SLICE):
+        r = OracleREWL(OracleConfig(L=L, n_win_E=2, n_win_M=1, overlap_E=0.5, walkers_per_window=2, seed=22))
+        _exact_pieces(r, lg, lambda win, e, m: np.where(win == 1, delta[m], 0.0), np.random.default_rng(7))
+        J, em, _ = r.join(rule)
+        out[rule] = (J, int(em[0]))
+    J1, p = out[oracle.JOIN_PER_SLICE]
+    assert np.array_equal(np.isfinite(J1), occ)
+    matched = occ & occ[p][None, :]          # bins of slices M occupied at E_mat
+    d1 = J1[matched] - lg[matched]
+    assert _spread(d1) < 1e-9
+    J0, p0 = out[oracle.JOIN_MARGINAL]
+    assert p0 == p
+    upper = matched & (np.arange(L * L + 1)[:, None] >= p)
+    assert _spread(J0[upper] - lg[upper]) > 0.1
+
+
+def test_per_slice_rule_removes_slice_offsets_M_join_L6():
+    """The same along M: two M windows (E unrestricted), the upper one offset
+    by a function of E alone; rule 1 rescales each E slice at M_mat."""
+    L = 6
+    g = oracle.transfer_gEM(L)
+    lg = _lg(g)
+    occ = g > 0
+    delta = np.random.default_rng(6).uniform(-0.3, 0.3, size=L * L + 1)
+    r = OracleREWL(OracleConfig(L=L, n_win_E=1, n_win_M=2, overlap_M=0.5, walkers_per_window=2, seed=23))
+    _exact_pieces(r, lg, lambda win, e, m: np.where(win == 1, delta[e], 0.0), np.random.default_rng(8))
+    J1, _, mm = r.join(oracle.JOIN_PER_SLICE)
+    q = int(mm[0])
+    matched = occ & occ[:, q][:, None]
+    assert np.array_equal(np.isfinite(J1), occ)
+    assert _spread(J1[matched] - lg[matched]) < 1e-9
+    J0, _, _ = r.join(oracle.JOIN_MARGINAL)
+    upper = matched & (np.arange(L * L + 1)[None, :] >= q)
+    assert _spread(J0[upper] - lg[upper]) > 0.1
