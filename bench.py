@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--form", default="batched", choices=["batched", "plain"],
                     help="plain: each walker's trials as a launch of their own (one thread, 4 streams), "
                          "exchange and check launched from the host, no graph; same trajectory")
+    ap.add_argument("--experiment", default=None, choices=["eq5"],
+                    help="eq5: serial WL vs the paper's REWL split at L = 8, Eq. 5 relative difference")
     ap.add_argument("--time-to", action="store_true",
                     help="run the workload to its final ln f and report the wall time and ln g error")
     return ap.parse_args()
@@ -269,7 +271,86 @@ def exact_lngE(L: int):
     return np.loadtxt(path)
 
 
+def exact_lngEM(L: int):
+    """Exact ln g(e, m) stored under tests/golden (transfer matrix), or None."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"gEM_L{L}.txt")
+    if not os.path.exists(path):
+        return None
+    g = np.loadtxt(path, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        return np.where(g > 0, np.log(np.where(g > 0, g, 1.0)), -np.inf)
+
+
 # ------------------------------------------------------------------- GPU ----
+
+def run_eq5(args):
+    """Sec. 3's comparison: serial WL over the whole (E, M) range with one
+    walker against REWL in the paper's split (3 E-windows, 50% overlap, 3
+    walkers per window), both to the same final ln f; the relative
+    difference of Eq. 5 between the two joint tables is computed on the
+    device.  Each run is capped at --max-seconds."""
+    import numpy as np
+    import torch
+
+    import paper_1508_02748_gb300 as P
+    from paper_1508_02748_gb300 import build as pkg_build
+
+    pkg_build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lnf_final = args.lnf_final if args.lnf_final is not None else 1e-6
+    prec = {"fp64": P.FP64, "f32x2": P.F32X2, "f32": P.F32}[args.precision]
+    out = {}
+    tables = {}
+    for key, w in (("serial_wl", workloads.SERIAL_L8), ("rewl", workloads.PAPER_L8)):
+        w = w.with_(lnf_final=lnf_final)
+        run = P.REWL(P.Config.from_workload(w, replicate=args.replicate, drive_budget=10**8, precision=prec),
+                     device=str(dev))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = run.status()
+        capped = False
+        while not st["done"]:
+            st = run.run_cycles(64)
+            if time.perf_counter() - t0 > args.max_seconds:
+                capped = True
+                break
+        elapsed = time.perf_counter() - t0
+        tables[key] = run.lng()
+        out[key] = {"workload": w.name, "seed": run.cfg.seed, "seconds": elapsed, "capped": capped,
+                    "iterations": st["iteration"], "lnf": st["lnf"], "trials_per_walker": st["trials"],
+                    "walkers": st["n_walkers"]}
+        run.close()
+    d = P.relative_difference(torch.from_numpy(tables["serial_wl"]).to(dev),
+                              torch.from_numpy(tables["rewl"]).to(dev)).cpu().numpy()
+    both = np.isfinite(tables["serial_wl"]) & np.isfinite(tables["rewl"])
+    B = d.shape[0]
+    e_idx = np.repeat(np.arange(B)[:, None], B, axis=1)
+    band = {}
+    for name, lo, hi in (("low_E_third", 0, B // 3), ("middle_third", B // 3, 2 * B // 3),
+                         ("high_E_third", 2 * B // 3, B)):
+        sel = both & (e_idx >= lo) & (e_idx < hi)
+        band[name] = float(d[sel].mean()) if sel.any() else None
+    ex = exact_lngEM(8)
+    vs_exact = {}
+    if ex is not None:
+        occ = np.isfinite(ex)
+        for key in tables:
+            de = P.relative_difference(torch.from_numpy(tables[key]).to(dev),
+                                       torch.from_numpy(ex).to(dev)).cpu().numpy()
+            vs_exact[key] = {"mean": float(np.nanmean(de[occ])), "max": float(np.nanmax(de[occ])),
+                             "support_equal": bool(np.array_equal(np.isfinite(tables[key]), occ))}
+    line = {"metric": "eq5_relative_difference_serial_wl_vs_rewl", "value": float(d[both].mean()),
+            "unit": "mean over bins occupied in both tables", "higher_is_better": False, "n_gpus": 1,
+            "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision], "data": "synthetic",
+            "config": {"workload": "eq5_L8_serial_vs_paper_split", "L": 8, "lnf_final": lnf_final,
+                       "max_seconds_per_run": args.max_seconds},
+            "max": float(d[both].max()), "median": float(np.median(d[both])), "bins": int(both.sum()),
+            "bins_in_one_table_only": int((np.isfinite(tables["serial_wl"]) ^ np.isfinite(tables["rewl"])).sum()),
+            "mean_by_energy": band, "vs_exact_joint": vs_exact, "runs": out}
+    print(json.dumps(line), flush=True)
+
 
 def run_gpu(args, w):
     import numpy as np
@@ -574,6 +655,10 @@ def main():
     w = workloads.ALL.get(args.workload)
     if args.precision is None and w is not None:
         args.precision = "fp64"
+    if args.experiment == "eq5":
+        args.precision = args.precision or "fp64"
+        run_eq5(args)
+        return
     if args.workload == workloads.BATCH_NAME:
         if args.precision is None or args.precision == "fp64":
             args.precision = "f32x2" if args.precision is None else args.precision

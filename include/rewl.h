@@ -65,6 +65,15 @@ extern "C" {
 /* What rewl_get_lng returns. */
 #define REWL_LNG_JOINED 0       /* (N+1) x (N+1) doubles, [e][m], sum g = 2^N */
 #define REWL_LNG_MARGINAL_E 1   /* N+1 doubles: ln sum_m g(e, m) of the joined table (Eq. 3) */
+/* Flag OR-ed into `what` of rewl_get_lng / rewl_get_lng_jackknife: the
+ * rescaling rule of each join step.  The paper rescales the surface at
+ * g(E_mat, M) (the sentence before Eq. 4), which admits two readings.  Default: one constant per piece,
+ * the difference of the two pieces' E marginals (Eq. 3) at E_mat (M
+ * marginals at M_mat when joining rows along M).  With this flag: one
+ * constant per M slice of the piece, ln g_i(E_mat, M) - ln g_j(E_mat, M),
+ * where both pieces have that bin, else the marginal constant (per E slice
+ * at M_mat along M). */
+#define REWL_JOIN_PER_SLICE 0x100
 
 typedef struct rewl_s rewl_t;   /* opaque */
 
@@ -188,7 +197,8 @@ int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t *host_H, si
 
 /* Final merge of each window's walkers, join (Eqs. 3-4, E then M) and
  * normalisation to sum g = 2^N, all on the device, copied to host_out.
- * what = REWL_LNG_JOINED or REWL_LNG_MARGINAL_E.  *needed gets the entry
+ * what = REWL_LNG_JOINED or REWL_LNG_MARGINAL_E, optionally OR
+ * REWL_JOIN_PER_SLICE (the rescaling rule).  *needed gets the entry
  * count; REWL_E_CAPACITY if capacity is smaller.  host_ematch (n_win_M x
  * (n_win_E - 1) int32) and host_mmatch (n_win_M - 1) receive the matching
  * points (-1 where unused) and may be NULL.  REWL_E_JOIN when two adjacent
@@ -196,8 +206,8 @@ int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t *host_H, si
 int rewl_get_lng(rewl_t *h, int what, double *host_out, size_t capacity, size_t *needed,
                  int32_t *host_ematch, int32_t *host_mmatch);
 
-/* Jackknife over the walkers of each window (Sec. 2: "jackknifing ... to
- * compute the statistical errors from a unique production run"): replicate k
+/* Jackknife over the walkers of each window (Sec. 2 proposes it for error
+ * bars from a single production run, the walkers being independent): replicate k
  * (k = 0..W-1) is the merge / join / normalisation of rewl_get_lng without
  * walker k of every window; host_mean gets the mean of the W replicates and
  * host_err sqrt((W-1)/W * sum_k (replicate_k - mean)^2), per entry, for
@@ -273,6 +283,17 @@ int rewl_batch_destroy(rewl_batch_t *b);
 int rewl_join_noalloc(const rewl_config *cfg, const double *d_lng, const int32_t *d_H, double *d_out,
                       void *stream);
 const char *rewl_noalloc_last_error(void);
+
+/* Relative difference of two density-of-states tables (Eq. 5, Sec. 3:
+ * the comparison of a serial WL and a REWL result):
+ * d_out[i] = |g_a - g_b| / ((g_a + g_b) / 2) computed from d_lng_a[i] =
+ * ln g_a and d_lng_b[i] = ln g_b (same normalisation, e.g. two outputs of
+ * rewl_get_lng); 2 where exactly one entry is -inf (empty), NaN where both
+ * are.  All three are device pointers to n doubles, owned by the caller;
+ * d_out may alias neither input.  Runs on `stream` and waits for it.
+ * Errors: REWL_E_INVALID (null pointer with n > 0), REWL_E_CUDA. */
+int rewl_relative_difference(const double *d_lng_a, const double *d_lng_b, double *d_out, uint64_t n,
+                             void *stream);
 
 /* Device Philox4x32-10 (the generator every random draw of the library uses;
  * Salmon et al., SC'11): d_out[4i..4i+3] = Philox(d_ctr[4i..4i+3], key).

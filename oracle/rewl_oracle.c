@@ -636,7 +636,7 @@ int orc_join_excl(const orc_rewl *s, int excl, double *out, int32_t *ematch, int
 }
 
 /* Rescaling rule of a join step (Eq. 4 and the sentence before it: the
- * surface is rescaled "at g(E_mat, M)").
+ * surface is rescaled at g(E_mat, M), read in two ways).
  *   rule 0: one constant per piece, the difference of the two pieces'
  *           marginals (Eq. 3) at the matching point;
  *   rule 1: one constant per slice: for every M of the piece, the

@@ -6,5 +6,6 @@ iteration advance, merge/join/normalisation) runs in the CUDA kernels of
 argument-marshalling binding.  Nothing is loaded at import time; the first
 :class:`REWL` loads the library and fails loudly if it is missing.
 """
-from .rewl import (F32, F32X2, FP64, LNG_JOINED, LNG_MARGINAL_E, PART_REST, PART_SAMPLE, PART_SAMPLE_PLAIN, REWL,  # noqa: F401
-                   SAMPLER_THREAD, SAMPLER_WARP, Batch, Config, REWLError, load_library, philox)
+from .rewl import (F32, F32X2, FP64, JOIN_MARGINAL, JOIN_PER_SLICE, LNG_JOINED, LNG_MARGINAL_E,  # noqa: F401
+                   PART_REST, PART_SAMPLE, PART_SAMPLE_PLAIN, REWL, SAMPLER_THREAD, SAMPLER_WARP, Batch, Config,
+                   REWLError, load_library, philox, relative_difference)

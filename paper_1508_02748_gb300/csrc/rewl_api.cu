@@ -114,6 +114,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     size_t st, rect, active, spins, we, wm, wt, wflat, lng, H;
     size_t piece, off, GE, eshift, efrom, eto, ematch, rowok, F, mshift, mfrom, mto, mmatch, J, red, marg, gbuf;
+    size_t eslice, mslice;
     size_t jk_ref, jk_sum, jk_sq, jk_mean, jk_err;
     size_t fail, total;
 };
@@ -194,6 +195,8 @@ Layout layout_of(const Dims &d)
     L.red = take(8 * 2048);
     L.marg = take(8 * B);
     L.gbuf = take(8 * 2 * B * (size_t)d.nM);
+    L.eslice = take(8 * (size_t)d.nwin * d.wM);
+    L.mslice = take(8 * (size_t)d.nM * B);
     L.jk_ref = take(8 * B * B);
     L.jk_sum = take(8 * B * B);
     L.jk_sq = take(8 * B * B);
@@ -391,6 +394,8 @@ int create_impl(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_
     j.red = (double *)(base + lay.red);
     j.marg = (double *)(base + lay.marg);
     j.gbuf = (double *)(base + lay.gbuf);
+    j.eslice = (double *)(base + lay.eslice);
+    j.mslice = (double *)(base + lay.mslice);
     j.jk_ref = (double *)(base + lay.jk_ref);
     j.jk_sum = (double *)(base + lay.jk_sum);
     j.jk_sq = (double *)(base + lay.jk_sq);
@@ -854,7 +859,9 @@ extern "C" int rewl_get_lng(rewl_t *h, int what, double *host_out, size_t capaci
                             int32_t *host_ematch, int32_t *host_mmatch)
 {
     if (!h) return REWL_E_INVALID;
-    const Params &p = h->p;
+    Params p = h->p;
+    p.join_rule = (what & REWL_JOIN_PER_SLICE) ? 1 : 0;
+    what &= ~REWL_JOIN_PER_SLICE;
     const size_t B = (size_t)p.N + 1;
     size_t n;
     if (what == REWL_LNG_JOINED) n = B * B;
@@ -883,7 +890,9 @@ extern "C" int rewl_get_lng_jackknife(rewl_t *h, int what, double *host_mean, do
                                       size_t *needed)
 {
     if (!h) return REWL_E_INVALID;
-    const Params &p0 = h->p;
+    Params p0 = h->p;
+    p0.join_rule = (what & REWL_JOIN_PER_SLICE) ? 1 : 0;
+    what &= ~REWL_JOIN_PER_SLICE;
     const size_t B = (size_t)p0.N + 1;
     size_t n;
     if (what == REWL_LNG_JOINED) n = B * B;
@@ -925,6 +934,17 @@ extern "C" int rewl_destroy(rewl_t *h)
         for (int i = 0; i <= REWL_PLAIN_STREAMS; ++i) cudaEventDestroy(h->plain_ev[i]);
     }
     delete h;
+    return REWL_OK;
+}
+
+extern "C" int rewl_relative_difference(const double *d_lng_a, const double *d_lng_b, double *d_out, uint64_t n,
+                                        void *stream)
+{
+    if (n && (!d_lng_a || !d_lng_b || !d_out)) return fail(nullptr, REWL_E_INVALID, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_rel_diff(d_lng_a, d_lng_b, d_out, (size_t)n, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(nullptr, REWL_E_CUDA, "relative difference: %s", cudaGetErrorString(e));
     return REWL_OK;
 }
 

@@ -79,6 +79,7 @@ struct Params {
     uint64_t drive_budget;
 
     int join_exclude; // merge: walker index within each window left out (-1: none)
+    int join_rule;    // join steps: 0 one constant per piece, 1 one per slice (rewl.h REWL_JOIN_PER_SLICE)
     int walker0;      // thread sampler: walker of thread 0 of block 0 (0 for a whole sweep)
 
     const int4 *rect;       // per window: e0, e1, m0, m1
@@ -112,6 +113,8 @@ struct JoinScratch {
     double *red;      // reduction scratch (>= 2 * 1024 doubles)
     double *marg;     // N+1 marginal output
     double *gbuf;     // nM x 2 x (N+1) work space of the E matching chains
+    double *eslice;   // nwin x wM: rule 1, shift of each M slice of each piece within its row
+    double *mslice;   // nM x (N+1): rule 1, shift of each E slice of each row
     double *jk_ref, *jk_sum, *jk_sq;   // jackknife accumulators, (N+1)^2 each
 };
 
@@ -127,6 +130,7 @@ cudaError_t launch_exchange(const Params &p, int max_pairs, cudaStream_t s);
 cudaError_t launch_flat(const Params &p, cudaStream_t s);
 cudaError_t launch_decide(const Params &p, int flags, cudaStream_t s);
 cudaError_t launch_reset(const Params &p, cudaStream_t s);
+cudaError_t launch_rel_diff(const double *a, const double *b, double *out, size_t n, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *d_ctr, uint32_t k0, uint32_t k1, uint32_t *d_out,
                           uint64_t n, cudaStream_t s);
 cudaError_t launch_tables_to_double(const Params &p, double *d_out, cudaStream_t s);

@@ -17,6 +17,8 @@
 // of exp/log and of the final parallel normalisation sum.
 #include <math.h>
 
+#include <math_constants.h>
+
 #include "rewl_internal.cuh"
 
 namespace rewl {
@@ -148,6 +150,8 @@ __global__ void k_match_e(Params p, JoinScratch j, double *gbuf)
     for (int a = first; a <= last; ++a)
         if (!p.active[b * nE + a]) { atomicExch(&p.st->join_error, 2); return; }
     double shift = 0.0;
+    if (p.join_rule == 1)
+        for (int ml = 0; ml < p.wM; ++ml) j.eslice[(size_t)(b * nE + first) * p.wM + ml] = 0.0;
     int from = p.rect[b * nE + first].x;
     for (int a = first; a <= last; ++a) {
         const int A = b * nE + a;
@@ -163,6 +167,18 @@ __global__ void k_match_e(Params p, JoinScratch j, double *gbuf)
             if (q < 0) { atomicExch(&p.st->join_error, 3); return; }
             j.ematch[b * (nE - 1) + a] = q;
             next_shift = shift + (Ga[q] - Gb[q]);
+            if (p.join_rule == 1) {
+                // the next piece's M slices: each matched at (E_mat, M) where
+                // both pieces have the bin, else by the marginals
+                const double *pa = j.piece + (size_t)A * p.tstride + (size_t)(q - RA.x) * p.wM;
+                const double *pb = j.piece + (size_t)(A + 1) * p.tstride + (size_t)(q - RB.x) * p.wM;
+                const double *sa = j.eslice + (size_t)A * p.wM;
+                double *sb = j.eslice + (size_t)(A + 1) * p.wM;
+                for (int ml = 0; ml < p.wM; ++ml) {
+                    const double va = pa[ml], vb = pb[ml];
+                    sb[ml] = sa[ml] + ((va != -INFINITY && vb != -INFINITY) ? va - vb : Ga[q] - Gb[q]);
+                }
+            }
             to = q;
         } else {
             to = RA.y + 1;
@@ -182,7 +198,8 @@ __device__ __forceinline__ double row_value(const Params &p, const JoinScratch &
             const int4 R = p.rect[A];
             if (m < R.z || m > R.w) return -INFINITY;
             const double v = j.piece[(size_t)A * p.tstride + (size_t)(e - R.x) * p.wM + (m - R.z)];
-            return v == -INFINITY ? v : v + j.eshift[A];
+            const double c = p.join_rule == 1 ? j.eslice[(size_t)A * p.wM + (m - R.z)] : j.eshift[A];
+            return v == -INFINITY ? v : v + c;
         }
     }
     return -INFINITY;
@@ -211,6 +228,8 @@ __global__ void k_match_m(Params p, JoinScratch j)
     if (first < 0) { atomicExch(&p.st->join_error, 4); return; }
     for (int b = first; b <= last; ++b) if (!j.rowok[b]) { atomicExch(&p.st->join_error, 5); return; }
     double shift = 0.0;
+    if (p.join_rule == 1)
+        for (int e = 0; e < B; ++e) j.mslice[(size_t)first * B + e] = 0.0;
     int from = p.rect[first * nE].z;
     for (int b = first; b <= last; ++b) {
         int to;
@@ -222,6 +241,12 @@ __global__ void k_match_m(Params p, JoinScratch j)
             if (q < 0) { atomicExch(&p.st->join_error, 6); return; }
             j.mmatch[b] = q;
             next_shift = shift + (Ga[q] - Gb[q]);
+            if (p.join_rule == 1)
+                for (int e = 0; e < B; ++e) {
+                    const double va = row_value(p, j, b, e, q), vb = row_value(p, j, b + 1, e, q);
+                    j.mslice[(size_t)(b + 1) * B + e] = j.mslice[(size_t)b * B + e]
+                        + ((va != -INFINITY && vb != -INFINITY) ? va - vb : Ga[q] - Gb[q]);
+                }
             to = q;
         } else {
             to = p.rect[b * nE].w + 1;
@@ -243,7 +268,8 @@ __global__ void k_assemble(Params p, JoinScratch j)
     for (int b = 0; b < p.nM; ++b) {
         if (m >= j.mfrom[b] && m < j.mto[b]) {
             const double r = row_value(p, j, b, e, m);
-            v = r == -INFINITY ? r : r + j.mshift[b];
+            const double c = p.join_rule == 1 ? j.mslice[(size_t)b * B + e] : j.mshift[b];
+            v = r == -INFINITY ? r : r + c;
             break;
         }
     }
@@ -376,6 +402,26 @@ cudaError_t launch_jk_accum(const JoinScratch &j, const double *x, size_t n, int
 cudaError_t launch_jk_final(const JoinScratch &j, double *mean, double *err, size_t n, int W, cudaStream_t s)
 {
     k_jk_final<<<256, 256, 0, s>>>(j, mean, err, n, W);
+    return cudaGetLastError();
+}
+
+// Eq. 5 per bin: |g_a - g_b| / ((g_a + g_b) / 2) = 2 tanh(|ln g_a - ln g_b| / 2),
+// 2 where one table is empty, NaN where both are.
+__global__ void k_rel_diff(const double *a, const double *b, double *out, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double x = a[i], y = b[i];
+        const bool ex = x == -CUDART_INF, ey = y == -CUDART_INF;
+        out[i] = (ex && ey) ? CUDART_NAN : (ex || ey) ? 2.0 : 2.0 * tanh(0.5 * fabs(x - y));
+    }
+}
+
+cudaError_t launch_rel_diff(const double *a, const double *b, double *out, size_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t want = (n + 255) / 256;
+    const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
+    k_rel_diff<<<blocks, 256, 0, s>>>(a, b, out, n);
     return cudaGetLastError();
 }
 

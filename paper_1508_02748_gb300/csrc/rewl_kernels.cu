@@ -336,8 +336,11 @@ cudaError_t launch_thread(const Params &p, int blocks, int wpb, uint64_t ntrials
 cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int wpb, cudaStream_t s)
 {
     if (p.sampler == REWL_SAMPLER_WARP) {
+        // staged exact tables fold their visit counts once per launch: fewer
+        // than 2^22 trials per launch keep every count exact in float
+        const uint64_t chunk = (p.smt && p.precision != REWL_F32) ? (1ull << 22) : (1ull << 30);
         while (ntrials > 0) {
-            const uint64_t n = ntrials > (1ull << 30) ? (1ull << 30) : ntrials;
+            const uint64_t n = ntrials > chunk ? chunk : ntrials;
             const cudaError_t e = launch_sweep_tree(p, n, p.group, wpb, p.smt != 0, s);
             if (e != cudaSuccess) return e;
             ntrials -= n;

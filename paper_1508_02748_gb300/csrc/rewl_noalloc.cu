@@ -142,6 +142,7 @@ extern "C" int rewl_join_noalloc(const rewl_config *cfg, const double *d_lng, co
     p.H = const_cast<int32_t *>(d_H);
     p.st = (DevState *)(base + o_st);
     JoinScratch j;
+    std::memset(&j, 0, sizeof j);            // rule-1 and jackknife buffers stay unused (null)
     j.piece = (double *)(base + o_piece);
     j.off = (double *)(base + o_off);
     j.GE = (double *)(base + o_GE);

@@ -86,6 +86,12 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     using Elem = typename TB::Elem;
     using Val = typename TB::Val;
     constexpr int DEPTH = TreeShape<G>::DEPTH;
+    // LAZY (tables staged in shared memory, exact formats): the staged ln g
+    // values stay those of the launch start and the shared H array counts the
+    // visits of this launch, Q(b); the value of bin b is table(b) + Q(b) ln f,
+    // folded into the tables once, when they are written back.  No
+    // floating-point update runs per trial (the double update is slow here).
+    constexpr bool LAZY = SMT && PREC != REWL_F32;
     constexpr int GPW = 32 / G;   // walkers per warp
     constexpr unsigned GBITS = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     if (SMT) {
         tl = reinterpret_cast<Elem *>(base + RING * sizeof(RingEntry) + sizeof(Mailbox) + ((nwords * 4 + 15) & ~15));
         tH = reinterpret_cast<int32_t *>(tl + T);
-        for (int k = gl; k < T; k += G) { tl[k] = g_tab[k]; tH[k] = gH[k]; }
+        for (int k = gl; k < T; k += G) { tl[k] = g_tab[k]; tH[k] = LAZY ? 0 : gH[k]; }
     } else {
         tl = g_tab;
         tH = gH;
@@ -145,8 +151,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     int e = p.we[w], m = p.wm[w];
     int ci = (e - R.x) * wM + (m - R.z);
     Val lbase = TB::load(tl, ci);   // table value of the current bin when entered
-    int lq = 0;                     // ln f steps since lbase
-    int hq = 0;                     // visits of the current bin not yet in H
+    int lq = 0;                     // ln f steps since lbase (LAZY: visits of this launch)
+    int hq = 0;                     // visits of the current bin not yet in H (LAZY: in Q)
     int hbase = tH[ci];
     float base32 = TB::approx(lbase);
     const unsigned long long t0 = p.wt[w];
@@ -189,7 +195,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             ufill = 2 * cfill - (unsigned)(t0 & 1ull);
             __syncwarp(gmask);
         }
-        if (lq >= (1 << 22)) {       // keep the float screen's counts exact
+        if (!LAZY && lq >= (1 << 22)) {   // keep the float screen's counts exact (LAZY
+                                          // launches run fewer than 2^22 trials)
             lbase = TB::add(lbase, lq, lnf, lnf32);
             lq = 0;
             base32 = TB::approx(lbase);
@@ -301,7 +308,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         const Val tc = TB::load(tl, cb), tn = TB::load(tl, nb);
         const Val cbase = c0b ? lbase : tc;
         const Val nbase = n0b ? lbase : tn;
-        const int ccnt = vcur + (c0b ? lq : 0), ncnt = vnew + (n0b ? lq : 0);
+        const int qc = LAZY ? tH[cb] : 0, qn = LAZY ? tH[nb] : 0;
+        const int ccnt = vcur + (c0b ? lq : qc), ncnt = vnew + (n0b ? lq : qn);
         const float cb32 = c0b ? base32 : TB::approx(tc);
         const float nb32 = n0b ? base32 : TB::approx(tn);
         const float c32 = __fmaf_rn((float)ccnt, lnf32, cb32);
@@ -377,13 +385,17 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
                 const int Xw = own ? after : ci;
                 const bool isci = Xw == ci;
                 const int cnt = own ? cntv : 0;
-                const Val v0 = isci ? lbase : TB::load(tl, Xw);
-                const int h0 = isci ? hbase : tH[Xw];
-                const int nv = cnt + (isci ? lq : 0), nh = cnt + (isci ? hq : 0);
-                const long long hv = (long long)(h0 < 0 ? 0 : h0) + nh;
-                if (hv > 0x7FFFFFFFll) err = 1;
-                tl[Xw] = TB::add(v0, nv, lnf, lnf32);
-                tH[Xw] = (int32_t)hv;
+                if (LAZY) {
+                    tH[Xw] = cnt + (isci ? lq : tH[Xw]);
+                } else {
+                    const Val v0 = isci ? lbase : TB::load(tl, Xw);
+                    const int h0 = isci ? hbase : tH[Xw];
+                    const int nv = cnt + (isci ? lq : 0), nh = cnt + (isci ? hq : 0);
+                    const long long hv = (long long)(h0 < 0 ? 0 : h0) + nh;
+                    if (hv > 0x7FFFFFFFll) err = 1;
+                    tl[Xw] = TB::add(v0, nv, lnf, lnf32);
+                    tH[Xw] = (int32_t)hv;
+                }
             }
         }
         // the group adopts the state after the last trial
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             hbase = tH[C];
             base32 = TB::approx(lbase);
             ci = C;
-            lq = cC;
+            lq = cC + (LAZY ? hbase : 0);
             hq = cC;
         }
         __syncwarp(gmask);
@@ -406,14 +418,32 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
 
     // ---- flush the current bin and the state
     if (gl == 0 && hq > 0) {
-        const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
-        if (hv > 0x7FFFFFFFll) err = 1;
-        tl[ci] = TB::add(lbase, lq, lnf, lnf32);
-        tH[ci] = (int32_t)hv;
+        if (LAZY) {
+            tH[ci] = lq;
+        } else {
+            const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
+            if (hv > 0x7FFFFFFFll) err = 1;
+            tl[ci] = TB::add(lbase, lq, lnf, lnf32);
+            tH[ci] = (int32_t)hv;
+        }
     }
     __syncwarp(gmask);
-    if (SMT)
+    if (LAZY) {
+        // fold the visits of this launch into the tables: bins not visited
+        // keep their values and H (never visited: -1)
+        for (int k = gl; k < T; k += G) {
+            const int q = tH[k];
+            if (q > 0) {
+                const int h0 = gH[k];
+                const long long hv = (long long)(h0 < 0 ? 0 : h0) + q;
+                if (hv > 0x7FFFFFFFll) err = 1;
+                g_tab[k] = TB::add(tl[k], q, lnf, lnf32);
+                gH[k] = (int32_t)hv;
+            }
+        }
+    } else if (SMT) {
         for (int k = gl; k < T; k += G) { g_tab[k] = tl[k]; gH[k] = tH[k]; }
+    }
     if (REG) {
         for (int r = gl; r < L; r += G)
             p.spins[(size_t)r * p.nwalk + w] = (uint32_t)(lat64 >> (r * L)) & (uint32_t)((1ull << L) - 1);

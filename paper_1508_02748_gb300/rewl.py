@@ -24,6 +24,7 @@ FP64, F32X2, F32 = 0, 1, 2
 PART_SAMPLE, PART_REST, PART_SAMPLE_PLAIN = 1, 2, 4
 SAMPLER_WARP, SAMPLER_THREAD = 0, 1
 LNG_JOINED, LNG_MARGINAL_E = 0, 1
+JOIN_MARGINAL, JOIN_PER_SLICE = 0, 0x100   # rescaling rule of a join step, OR-ed into `what`
 
 
 class REWLError(RuntimeError):
@@ -79,6 +80,7 @@ SIGNATURES = {
     "rewl_last_error": (ctypes.c_char_p, [_P]),
     "rewl_destroy": (ctypes.c_int, [_P]),
     "rewl_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P]),
+    "rewl_relative_difference": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P]),
     "rewl_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "rewl_batch_cycles_per_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "rewl_batch_run_cycles": (ctypes.c_int, [_P, ctypes.c_uint64]),
@@ -260,9 +262,12 @@ class REWL:
         H = np.ascontiguousarray(H, dtype=np.int32)
         _check(load_library().rewl_set_tables(self._h, lng.ctypes.data, H.ctypes.data, lng.size), self._h)
 
-    def lng(self, what: int = LNG_JOINED, matches: bool = False):
+    def lng(self, what: int = LNG_JOINED, matches: bool = False, rule: int = JOIN_MARGINAL):
+        """Joined ln g (or its E marginal); rule JOIN_PER_SLICE rescales each
+        slice at the matching point instead of each piece as a whole."""
         B = self.N + 1
         n = B * B if what == LNG_JOINED else B
+        what = what | rule
         out = np.zeros(n, dtype=np.float64)
         need = ctypes.c_size_t(0)
         nE, nM = self.cfg.n_win_E, self.cfg.n_win_M
@@ -270,19 +275,21 @@ class REWL:
         mm = np.zeros(max(1, nM - 1), dtype=np.int32)
         _check(load_library().rewl_get_lng(self._h, what, out.ctypes.data, n, ctypes.byref(need),
                                            em.ctypes.data, mm.ctypes.data), self._h)
-        out = out.reshape(B, B) if what == LNG_JOINED else out
+        out = out.reshape(B, B) if n == B * B else out
         return (out, em, mm) if matches else out
 
-    def jackknife(self, what: int = LNG_JOINED):
+    def jackknife(self, what: int = LNG_JOINED, rule: int = JOIN_MARGINAL):
         """Jackknife mean and error of ln g over the walkers of each window."""
         B = self.N + 1
         n = B * B if what == LNG_JOINED else B
+        joined = what == LNG_JOINED
+        what = what | rule
         mean = np.zeros(n, dtype=np.float64)
         err = np.zeros(n, dtype=np.float64)
         need = ctypes.c_size_t(0)
         _check(load_library().rewl_get_lng_jackknife(self._h, what, mean.ctypes.data, err.ctypes.data, n,
                                                      ctypes.byref(need)), self._h)
-        if what == LNG_JOINED:
+        if joined:
             return mean.reshape(B, B), err.reshape(B, B)
         return mean, err
 
@@ -340,6 +347,23 @@ def philox(counters, key) -> "object":
     _check(load_library().rewl_philox(ctypes.c_void_p(c.data_ptr()), k.ctypes.data,
                                       ctypes.c_void_p(out.data_ptr()), c.shape[0],
                                       ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+def relative_difference(lng_a, lng_b) -> "object":
+    """Eq. 5 per bin on the device: |g_a - g_b| / ((g_a + g_b) / 2) from two
+    float64 CUDA tensors of ln g of the same shape (2 where one is empty,
+    NaN where both are)."""
+    import torch
+    a = lng_a.contiguous()
+    b = lng_b.contiguous()
+    if a.shape != b.shape or a.dtype != torch.float64 or b.dtype != torch.float64 or not a.is_cuda or b.device != a.device:
+        raise ValueError("two float64 CUDA tensors of one shape on one device expected")
+    out = torch.empty_like(a)
+    s = torch.cuda.current_stream(a.device)
+    _check(load_library().rewl_relative_difference(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr()), a.numel(),
+                                                   ctypes.c_void_p(s.cuda_stream)))
     return out
 
 

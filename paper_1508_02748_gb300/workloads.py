@@ -52,6 +52,14 @@ REWL_L32 = Workload("rewl_L32_16x4_w32", 32, 16, 4, 0.75, 0.75, 32, 1.0, 1e-6, 0
 # Precision study: L=64, 32x8 windows at 75% overlap, 16 walkers per window, ln f down to 1e-8.
 REWL_L64 = Workload("rewl_L64_32x8_w16", 64, 32, 8, 0.75, 0.75, 16, 1.0, 1e-8, 0.5, 0.8, 10_000, 16, 4)
 
+# The paper's own runs (Sec. 3): E split into 3 equal windows at 50% overlap,
+# M unrestricted, 3 walkers per window, ln f down to 1e-8; L = 8 and 16.
+PAPER_L8 = Workload("paper_L8_E3_o50_w3", 8, 3, 1, 0.5, 0.5, 3, 1.0, 1e-8, 0.5, 0.8, 10_000, 1, 6)
+PAPER_L16 = Workload("paper_L16_E3_o50_w3", 16, 3, 1, 0.5, 0.5, 3, 1.0, 1e-8, 0.5, 0.8, 10_000, 1, 7)
+# Serial 2D WL over the whole (E, M) range at L = 8, one walker (the
+# reference of the Eq. 5 comparison in Sec. 3).
+SERIAL_L8 = Workload("serial_wl_L8", 8, 1, 1, 0.5, 0.5, 1, 1.0, 1e-8, 0.5, 0.8, 10_000, 1, 8)
+
 # Uneven batch: 24 independent REWL runs, six each of L = 16, 24, 32, 48 with
 # window grids and walkers per window scaled to L (4x2/32, 8x2/16, 12x4/16,
 # 16x4/8; 10,752 walkers in all), 75% overlap, ln f down to 1e-6.
@@ -69,4 +77,4 @@ def mixed_batch() -> list:
 
 BATCH_NAME = "batch_24_mixed_L16_24_32_48"
 
-ALL = {w.name: w for w in (SERIAL_L4, REWL_L8, REWL_L32, REWL_L64)}
+ALL = {w.name: w for w in (SERIAL_L4, REWL_L8, REWL_L32, REWL_L64, PAPER_L8, PAPER_L16, SERIAL_L8)}
