@@ -62,12 +62,21 @@ struct RingEntry {
 // Per-walker exchange area of one step (shared memory): the lanes of a
 // group trade their trial results through it instead of warp shuffles.
 struct Mailbox {
-    int move[32];                  // packed (de, dm) of each lane's own trial
     int after[8];                  // bin after trial t+k on the true path
     int leafpos;                   // the leaf's new (e, m)
     int pad;
     unsigned long long flips;      // register lattice: the path's flip mask
 };
+
+// Eq. 1 decided in double from the exact values (near-ties of the float
+// screen only); kept out of line so none of it runs in the common case.
+template <class TB>
+__device__ __noinline__ int exact_accept(typename TB::Val cbase, int ccnt, typename TB::Val nbase, int ncnt,
+                                         double lnf, uint32_t xu)
+{
+    const double delta = fma((double)ccnt, lnf, TB::exact(cbase)) - fma((double)ncnt, lnf, TB::exact(nbase));
+    return (delta >= 0.0 || log(unit_open_d(xu)) < delta) ? 1 : 0;
+}
 
 template <int G>
 struct TreeShape {
@@ -146,6 +155,17 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     int srck[DEPTH];
     #pragma unroll
     for (int k = 0; k < DEPTH; ++k) srck[k] = (1 << k) - 1 + (hist & ((1 << k) - 1));
+    // the lane is on the true path iff the ballot bits of its ancestors
+    // (lane 2^k - 1 + (h mod 2^k) at depth k < d) are the outcomes its
+    // history assumes: anc marks the ancestors, want holds those outcomes
+    unsigned anc = 0, want = 0;
+    #pragma unroll
+    for (int k = 0; k <= DEPTH; ++k)
+        if (k < dl) {
+            const int a = (1 << k) - 1 + (hist & ((1 << k) - 1));
+            anc |= 1u << a;
+            want |= (unsigned)((hist >> k) & 1) << a;
+        }
 
     // committed state (uniform over the group)
     int e = p.we[w], m = p.wm[w];
@@ -251,46 +271,23 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         const int dm_own = sbit ? -1 : 1;
         const int pack = (de_own + 2) | ((dm_own + 1) << 3);
 
-        // ---- 2. the history's earlier trials: moves from the lanes that took them
-        // (shared lattice) or recomputed (register lattice); a history that
-        // accepts a move out of the window is never the true path, and its
-        // bins are clamped below only to keep its reads in bounds
+        // ---- 2. the history's earlier trials: the move of trial k under the
+        // history's first k outcomes is the own move of lane 2^k - 1 + (h mod 2^k),
+        // taken by shuffle; a history that accepts a move out of the window is
+        // never the true path, and its bins are clamped below only to keep its
+        // reads in bounds
         int ce = e, cm = m, cbin = ci;
         int vb[DEPTH];               // bin after each earlier trial (-1 past the own depth)
-        if (REG) {
-            // register lattice: recompute the moves the history accepts (the
-            // lattice under the history's earlier flips), no exchange needed
-            unsigned long long Fk = 0;
-            #pragma unroll
-            for (int k = 0; k < DEPTH; ++k) {
-                if (k < dl && ((hist >> k) & 1)) {
-                    const unsigned long long v = lat64 ^ Fk;
-                    const uint32_t a = sa[k];
-                    const uint32_t sk = (uint32_t)(v >> (a & 63u)) & 1u;
-                    const int nk = (int)(((uint32_t)(v >> ((a >> 6) & 63u)) & 1u) + ((uint32_t)(v >> ((a >> 12) & 63u)) & 1u)
-                                       + ((uint32_t)(v >> ((a >> 18) & 63u)) & 1u) + ((uint32_t)(v >> ((a >> 24) & 63u)) & 1u));
-                    const int de = sk ? nk - 2 : 2 - nk, dm = sk ? -1 : 1;
-                    ce += de;
-                    cm += dm;
-                    cbin += de * wM + dm;
-                    Fk ^= 1ull << (a & 63u);
-                }
-                vb[k] = k < dl ? cbin : -1;
+        #pragma unroll
+        for (int k = 0; k < DEPTH; ++k) {
+            const int pk = __shfl_sync(gmask, pack, grp * G + srck[k]);
+            if (k < dl && ((hist >> k) & 1)) {
+                const int de = (pk & 7) - 2, dm = ((pk >> 3) & 3) - 1;
+                ce += de;
+                cm += dm;
+                cbin += de * wM + dm;
             }
-        } else {
-            box->move[gl] = pack;
-            __syncwarp(gmask);
-            #pragma unroll
-            for (int k = 0; k < DEPTH; ++k) {
-                const int pk = box->move[srck[k]];
-                if (k < dl && ((hist >> k) & 1)) {
-                    const int de = (pk & 7) - 2, dm = ((pk >> 3) & 3) - 1;
-                    ce += de;
-                    cm += dm;
-                    cbin += de * wM + dm;
-                }
-                vb[k] = k < dl ? cbin : -1;
-            }
+            vb[k] = k < dl ? cbin : -1;
         }
 
         // ---- 3. decision of the own trial (Eq. 1)
@@ -321,25 +318,14 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             // plain float: the values the walker sees are the rounded sums
             acc = (me.lnu < TB::add(cbase, ccnt, lnf, lnf32) - TB::add(nbase, ncnt, lnf, lnf32)) ? 1 : 0;
         } else if (live && !acc && !(me.lnu > d32 + M)) {
-            const double delta = fma((double)ccnt, lnf, TB::exact(cbase)) - fma((double)ncnt, lnf, TB::exact(nbase));
-            acc = (delta >= 0.0 || log(unit_open_d(me.xu)) < delta) ? 1 : 0;
+            acc = exact_accept<TB>(cbase, ccnt, nbase, ncnt, lnf, me.xu);
         }
         acc = live ? acc : 0;
         const int after = acc ? nbin : cbin;   // bin after the own trial, under the own history
 
-        // ---- the true path, walked from the root over the ballot (children of
-        // lane l at depth k are l + 2^k (reject) and l + 2^(k+1) (accept))
+        // ---- the true path: the lanes whose ancestors decided as their history assumes
         const unsigned bal = (__ballot_sync(gmask, acc) >> (grp * G)) & GBITS;
-        int path = 0, node = 0;
-        #pragma unroll
-        for (int k = 0; k <= DEPTH; ++k) {
-            if (k <= D) {
-                const int bk = (int)((bal >> node) & 1u);
-                path |= bk << k;
-                node += (1 + bk) << k;
-            }
-        }
-        const bool onp = dl <= D && hist == (path & ((1 << dl) - 1));
+        const bool onp = dl <= D && ((bal ^ want) & anc) == 0u;
         const bool is_leaf = onp && dl == D;
 
         // ---- commit: the on-path lane of depth k takes trial t+k
