@@ -387,16 +387,17 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         // the group adopts the state after the last trial
         e = ne;
         m = nm;
-        if (C == ci) {
-            lq += cC;
-            hq += cC;
-        } else {
-            lbase = TB::load(tl, C);
-            hbase = tH[C];
-            base32 = TB::approx(lbase);
+        {
+            const bool same = C == ci;
+            const Val lC = TB::load(tl, C);
+            const int hC = tH[C];
+            const float bC = TB::approx(lC);
+            lbase = same ? lbase : lC;
+            hbase = same ? hbase : hC;
+            base32 = same ? base32 : bC;
+            lq = same ? lq + cC : cC + (LAZY ? hC : 0);
+            hq = same ? hq + cC : cC;
             ci = C;
-            lq = cC + (LAZY ? hbase : 0);
-            hq = cC;
         }
         __syncwarp(gmask);
         u += (unsigned)(D + 1);
