@@ -78,6 +78,15 @@ __device__ __noinline__ int exact_accept(typename TB::Val cbase, int ccnt, typen
     return (delta >= 0.0 || log(unit_open_d(xu)) < delta) ? 1 : 0;
 }
 
+// The same with staged tables that keep their launch-start values: the base
+// values are read from the staged table here, off the common path.
+template <class TB>
+__device__ __noinline__ int exact_accept_staged(const typename TB::Elem *tl, int cb, int ccnt, int nb, int ncnt,
+                                                double lnf, uint32_t xu)
+{
+    return exact_accept<TB>(TB::load(tl, cb), ccnt, TB::load(tl, nb), ncnt, lnf, xu);
+}
+
 template <int G>
 struct TreeShape {
     static constexpr int DEPTH = G == 32 ? 4 : G == 16 ? 3 : G == 8 ? 2 : 1;
@@ -128,6 +137,10 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         tl = reinterpret_cast<Elem *>(base + RING * sizeof(RingEntry) + sizeof(Mailbox) + ((nwords * 4 + 15) & ~15));
         tH = reinterpret_cast<int32_t *>(tl + T);
         for (int k = gl; k < T; k += G) { tl[k] = g_tab[k]; tH[k] = LAZY ? 0 : gH[k]; }
+        if constexpr (LAZY && PREC == REWL_FP64) {
+            float *t32 = reinterpret_cast<float *>(tH + T);
+            for (int k = gl; k < T; k += G) t32[k] = TB::approx(g_tab[k]);
+        }
     } else {
         tl = g_tab;
         tH = gH;
@@ -170,6 +183,12 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     // committed state (uniform over the group)
     int e = p.we[w], m = p.wm[w];
     int ci = (e - R.x) * wM + (m - R.z);
+    // LAZY: the float screen reads one 32-bit word per bin: the float copy of
+    // a double table (staged after H), the hi word of a compensated pair
+    const float *scr32 = !LAZY ? nullptr
+                       : (PREC == REWL_FP64) ? reinterpret_cast<const float *>(tH + T)
+                                             : reinterpret_cast<const float *>(tl);
+    constexpr int SCR_STRIDE = PREC == REWL_FP64 ? 1 : 2;
     Val lbase = TB::load(tl, ci);   // table value of the current bin when entered
     int lq = 0;                     // ln f steps since lbase (LAZY: visits of this launch)
     int hq = 0;                     // visits of the current bin not yet in H (LAZY: in Q)
@@ -302,13 +321,20 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             vnew += (vb[k] == nb);
         }
         const bool c0b = cb == ci, n0b = nb == ci;
-        const Val tc = TB::load(tl, cb), tn = TB::load(tl, nb);
-        const Val cbase = c0b ? lbase : tc;
-        const Val nbase = n0b ? lbase : tn;
+        Val cbase, nbase;
+        float cb32, nb32;
+        if constexpr (LAZY) {
+            cb32 = c0b ? base32 : scr32[cb * SCR_STRIDE];
+            nb32 = n0b ? base32 : scr32[nb * SCR_STRIDE];
+        } else {
+            const Val tc = TB::load(tl, cb), tn = TB::load(tl, nb);
+            cbase = c0b ? lbase : tc;
+            nbase = n0b ? lbase : tn;
+            cb32 = c0b ? base32 : TB::approx(tc);
+            nb32 = n0b ? base32 : TB::approx(tn);
+        }
         const int qc = LAZY ? tH[cb] : 0, qn = LAZY ? tH[nb] : 0;
         const int ccnt = vcur + (c0b ? lq : qc), ncnt = vnew + (n0b ? lq : qn);
-        const float cb32 = c0b ? base32 : TB::approx(tc);
-        const float nb32 = n0b ? base32 : TB::approx(tn);
         const float c32 = __fmaf_rn((float)ccnt, lnf32, cb32);
         const float n32 = __fmaf_rn((float)ncnt, lnf32, nb32);
         const float d32 = c32 - n32;
@@ -318,7 +344,9 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             // plain float: the values the walker sees are the rounded sums
             acc = (me.lnu < TB::add(cbase, ccnt, lnf, lnf32) - TB::add(nbase, ncnt, lnf, lnf32)) ? 1 : 0;
         } else if (live && !acc && !(me.lnu > d32 + M)) {
-            acc = exact_accept<TB>(cbase, ccnt, nbase, ncnt, lnf, me.xu);
+            // LAZY: the current bin's base is its staged value too (lbase == tl[ci])
+            if constexpr (LAZY) acc = exact_accept_staged<TB>(tl, cb, ccnt, nb, ncnt, lnf, me.xu);
+            else acc = exact_accept<TB>(cbase, ccnt, nbase, ncnt, lnf, me.xu);
         }
         acc = live ? acc : 0;
         const int after = acc ? nbin : cbin;   // bin after the own trial, under the own history
@@ -389,10 +417,15 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         m = nm;
         {
             const bool same = C == ci;
-            const Val lC = TB::load(tl, C);
             const int hC = tH[C];
-            const float bC = TB::approx(lC);
-            lbase = same ? lbase : lC;
+            float bC;
+            if constexpr (LAZY) {
+                bC = scr32[C * SCR_STRIDE];
+            } else {
+                const Val lC = TB::load(tl, C);
+                bC = TB::approx(lC);
+                lbase = same ? lbase : lC;
+            }
             hbase = same ? hbase : hC;
             base32 = same ? base32 : bC;
             lq = same ? lq + cC : cC + (LAZY ? hC : 0);
@@ -447,11 +480,12 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
 }
 
 // Shared memory per walker: ring, mailbox, lattice (16-byte padded) and, when staged,
-// the tables (8-byte ln g entries in either format, 4-byte H).
+// the tables (8-byte ln g entries in either format, 4-byte H, and for double
+// tables a 4-byte float copy the screen reads).
 size_t tree_smem_per_warp(const Params &p, bool smt)
 {
     size_t b = RING * sizeof(RingEntry) + sizeof(Mailbox) + (((size_t)p.nwords * 4 + 15) & ~(size_t)15);
-    if (smt) b += (size_t)p.T * (8 + sizeof(int32_t));
+    if (smt) b += (size_t)p.T * (8 + sizeof(int32_t) + (p.precision == REWL_FP64 ? sizeof(float) : 0));
     return (b + 15) & ~(size_t)15;
 }
 
