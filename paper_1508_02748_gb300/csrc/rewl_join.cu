@@ -78,25 +78,43 @@ __device__ int match_point(const double *Ga, const double *Gb, int lo, int hi, i
 
 }  // namespace
 
-// 1a. Offsets: one thread per (window, walker), bins in order, relative to
-// the first walker taking part (walker join_exclude, if >= 0, is left out:
-// the jackknife replicates).
-__global__ void k_merge_off(Params p, JoinScratch j)
+// 1a. Offsets: one block per (window, walker), relative to the first walker
+// taking part (walker join_exclude, if >= 0, is left out: the jackknife
+// replicates).  The block's threads take the bins in strides and reduce
+// their sums in a fixed order.
+constexpr int MERGE_OFF_THREADS = 256;
+
+__global__ void __launch_bounds__(MERGE_OFF_THREADS) k_merge_off(Params p, JoinScratch j)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = blockIdx.x;
     if (idx >= p.nwalk) return;
     const int win = idx / p.W, k = idx % p.W;
     if (!p.active[win]) return;
     const int ref = p.join_exclude == 0 ? 1 : 0;   // the first walker taking part
-    if (k == ref || k == p.join_exclude) { j.off[idx] = 0.0; return; }
+    if (k == ref || k == p.join_exclude) {
+        if (threadIdx.x == 0) j.off[idx] = 0.0;
+        return;
+    }
     const size_t b0 = (size_t)(win * p.W + ref) * p.tstride, bk = (size_t)idx * p.tstride;
     double acc = 0.0;
     long long common = 0;
-    for (int i = 0; i < p.T; ++i) {
+    for (int i = threadIdx.x; i < p.T; i += MERGE_OFF_THREADS) {
         if (!all_seen(p, win, i)) continue;
         acc += lng_at(p, bk + i) - lng_at(p, b0 + i);
         ++common;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+        common += __shfl_down_sync(0xFFFFFFFFu, common, o);
+    }
+    __shared__ double s_acc[MERGE_OFF_THREADS / 32];
+    __shared__ long long s_cnt[MERGE_OFF_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) { s_acc[threadIdx.x >> 5] = acc; s_cnt[threadIdx.x >> 5] = common; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    acc = 0.0;
+    common = 0;
+    for (int w = 0; w < MERGE_OFF_THREADS / 32; ++w) { acc += s_acc[w]; common += s_cnt[w]; }
     if (common == 0) { atomicExch(&p.st->join_error, 1); j.off[idx] = 0.0; return; }
     j.off[idx] = acc / (double)common;
 }
@@ -324,7 +342,7 @@ __global__ void k_normalise(double *v, size_t n, const double *red_max, const do
 cudaError_t launch_join(const Params &p, const JoinScratch &j, cudaStream_t s)
 {
     const int B = p.N + 1;
-    k_merge_off<<<(p.nwalk + 127) / 128, 128, 0, s>>>(p, j);
+    k_merge_off<<<p.nwalk, MERGE_OFF_THREADS, 0, s>>>(p, j);
     const size_t nb = (size_t)p.nwin * p.T;
     k_merge<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(p, j);
     k_marg_piece<<<(p.nwin * p.wE + 127) / 128, 128, 0, s>>>(p, j);

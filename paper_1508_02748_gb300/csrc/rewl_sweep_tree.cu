@@ -68,23 +68,33 @@ struct Mailbox {
     unsigned long long flips;      // register lattice: the path's flip mask
 };
 
-// Eq. 1 decided in double from the exact values (near-ties of the float
-// screen only); kept out of line so none of it runs in the common case.
+// Eq. 1 decided from the exact values (near-ties of the float screen only);
+// kept out of line so none of it runs in the common case.  The difference
+// delta is exact in double.  The float ln u of the ring (logf of u rounded to
+// float) is within 2^-22 (|ln u| + 1) of ln u: u rounds with relative error
+// below 2^-23 and logf errs by at most 1 ulp (its documented bound).  So
+// outside a band 4x wider the float ln u decides, and only inside it is ln u
+// taken in double (the double logarithm is slow here).
 template <class TB>
 __device__ __noinline__ int exact_accept(typename TB::Val cbase, int ccnt, typename TB::Val nbase, int ncnt,
-                                         double lnf, uint32_t xu)
+                                         double lnf, uint32_t xu, float lnu32)
 {
     const double delta = fma((double)ccnt, lnf, TB::exact(cbase)) - fma((double)ncnt, lnf, TB::exact(nbase));
-    return (delta >= 0.0 || log(unit_open_d(xu)) < delta) ? 1 : 0;
+    if (delta >= 0.0) return 1;
+    const double lu = (double)lnu32;
+    const double band = (fabs(lu) + 1.0) * 0x1p-20;
+    if (lu < delta - band) return 1;
+    if (lu > delta + band) return 0;
+    return log(unit_open_d(xu)) < delta ? 1 : 0;
 }
 
 // The same with staged tables that keep their launch-start values: the base
 // values are read from the staged table here, off the common path.
 template <class TB>
 __device__ __noinline__ int exact_accept_staged(const typename TB::Elem *tl, int cb, int ccnt, int nb, int ncnt,
-                                                double lnf, uint32_t xu)
+                                                double lnf, uint32_t xu, float lnu32)
 {
-    return exact_accept<TB>(TB::load(tl, cb), ccnt, TB::load(tl, nb), ncnt, lnf, xu);
+    return exact_accept<TB>(TB::load(tl, cb), ccnt, TB::load(tl, nb), ncnt, lnf, xu, lnu32);
 }
 
 template <int G>
@@ -345,8 +355,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             acc = (me.lnu < TB::add(cbase, ccnt, lnf, lnf32) - TB::add(nbase, ncnt, lnf, lnf32)) ? 1 : 0;
         } else if (live && !acc && !(me.lnu > d32 + M)) {
             // LAZY: the current bin's base is its staged value too (lbase == tl[ci])
-            if constexpr (LAZY) acc = exact_accept_staged<TB>(tl, cb, ccnt, nb, ncnt, lnf, me.xu);
-            else acc = exact_accept<TB>(cbase, ccnt, nbase, ncnt, lnf, me.xu);
+            if constexpr (LAZY) acc = exact_accept_staged<TB>(tl, cb, ccnt, nb, ncnt, lnf, me.xu, me.lnu);
+            else acc = exact_accept<TB>(cbase, ccnt, nbase, ncnt, lnf, me.xu, me.lnu);
         }
         acc = live ? acc : 0;
         const int after = acc ? nbin : cbin;   // bin after the own trial, under the own history
