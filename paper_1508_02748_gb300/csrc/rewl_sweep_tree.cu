@@ -62,6 +62,7 @@ struct RingEntry {
 // Per-walker exchange area of one step (shared memory): the lanes of a
 // group trade their trial results through it instead of warp shuffles.
 struct Mailbox {
+    int dummy[32];                 // discarded stores of the branch-free write-back
     int after[8];                  // bin after trial t+k on the true path
     int leafpos;                   // the leaf's new (e, m)
     int pad;
@@ -405,21 +406,25 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         {
             const bool own = onp && firstv && after != C;
             const bool entry_left = gl == G - 1 && C != ci && !b0_seen && hq > 0;
-            if (own || entry_left) {
+            if (LAZY) {
+                // branch-free: lanes with nothing to write store to their own
+                // slot of the mailbox (the bin index is clamped because a lane
+                // off the true path may hold a bin outside the window)
+                const int Xw = min(max(own ? after : ci, 0), T - 1);
+                const int nq = (own ? cntv : 0) + (Xw == ci ? lq : tH[Xw]);
+                int *dst = (own || entry_left) ? &tH[Xw] : &box->dummy[gl];
+                *dst = nq;
+            } else if (own || entry_left) {
                 const int Xw = own ? after : ci;
                 const bool isci = Xw == ci;
                 const int cnt = own ? cntv : 0;
-                if (LAZY) {
-                    tH[Xw] = cnt + (isci ? lq : tH[Xw]);
-                } else {
-                    const Val v0 = isci ? lbase : TB::load(tl, Xw);
-                    const int h0 = isci ? hbase : tH[Xw];
-                    const int nv = cnt + (isci ? lq : 0), nh = cnt + (isci ? hq : 0);
-                    const long long hv = (long long)(h0 < 0 ? 0 : h0) + nh;
-                    if (hv > 0x7FFFFFFFll) err = 1;
-                    tl[Xw] = TB::add(v0, nv, lnf, lnf32);
-                    tH[Xw] = (int32_t)hv;
-                }
+                const Val v0 = isci ? lbase : TB::load(tl, Xw);
+                const int h0 = isci ? hbase : tH[Xw];
+                const int nv = cnt + (isci ? lq : 0), nh = cnt + (isci ? hq : 0);
+                const long long hv = (long long)(h0 < 0 ? 0 : h0) + nh;
+                if (hv > 0x7FFFFFFFll) err = 1;
+                tl[Xw] = TB::add(v0, nv, lnf, lnf32);
+                tH[Xw] = (int32_t)hv;
             }
         }
         // the group adopts the state after the last trial
