@@ -17,11 +17,19 @@
 //      and walks them to find its current bin and the bins visited;
 //   3. decides its own trial (Eq. 1) with the exact ln g values the sequential
 //      chain would see there: value(bin) = table(bin) + visits * ln f.
-// One ballot gives the true path from the root.  The path and the trial
-// sites are then known to every lane, and lane k of the path knows the bin
-// the walker is in after trial t+k; after five shuffles, lane k commits
+// One ballot gives the true path from the root: a lane is on it iff the
+// ballot bits of its ancestors are the outcomes its history assumes.  Lane k
+// of the path knows the bin the walker is in after trial t+k and posts it in
+// a per-walker mailbox in shared memory; after one warp barrier every lane
+// knows the path's bins, the leaf's (E, M) and its flips, and lane k commits
 // trial k: its spin flip, and the ln g / H update of its bin if that bin is
 // left in this step (first occurrence only, with all its visits).
+//
+// Tables staged in shared memory (double or compensated pairs) are not
+// updated during a launch: H counts the launch's visits Q(b), a bin's value
+// is table(b) + Q(b) ln f, and the counts are folded into the tables when
+// the launch writes them back.  The float screen reads a 32-bit copy of each
+// staged value.
 //
 // The outcome is the sequential chain itself, trial for trial:
 //   - random numbers are drawn per trial index from the TRIAL stream of
@@ -34,7 +42,9 @@
 //     within the exact range of the format;
 //   - decisions are screened in float with a margin that bounds the float
 //     rounding (|x - float(x)| < 2^-23 |x| for both table formats) and
-//     re-taken in double on near-ties.
+//     re-taken exactly on near-ties (out of line: the exact difference
+//     against the float ln u, and ln u in double only when those two are
+//     within 2^-20 (|ln u| + 1)).
 // The walker's current bin stays in registers (its table value at entry,
 // the visits since then) and is written back when the walker leaves it.
 #include "rewl_tab.cuh"
