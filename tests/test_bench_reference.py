@@ -1,0 +1,45 @@
+"""bench.py's reference arm (the CPU oracle) on CPU: one JSON line with the
+keys the benchmark contract names, on the same metric, unit and workload as
+the GPU arm, and a refusal to run the batch workload's ~35 GB of tables."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(*args):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    import bench
+    d = _run("--impl", "reference", "--steps", "2", "--warmup", "3")
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == "trials/s" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["config"]["workload"] == "rewl_L8_3x3_w4"
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    # 2 cycles x 10^4 trials x 36 walkers in the reported time
+    assert abs(d["value"] * d["ms_per_step"] * 2 / 1e3 - 2 * 10_000 * 36) < 1e-3 * 2 * 10_000 * 36
+
+
+def test_reference_arm_warmup_floor():
+    d = _run("--impl", "reference", "--steps", "1", "--warmup", "0")
+    assert d["warmup"] >= 3
+
+
+def test_reference_arm_refuses_batch():
+    d = _run("--impl", "reference", "--workload", "batch_24_mixed_L16_24_32_48", "--steps", "1")
+    assert d["impl"] == "reference" and "unavailable" in d
