@@ -81,6 +81,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tiling")
+    ap.add_argument("--lanes", type=int, default=None, choices=[8, 16, 32],
+                    help="warp sampler: lanes per walker (fixes the tiling, no autotuning)")
+    ap.add_argument("--wpb", type=int, default=None,
+                    help="warps (warp sampler) or threads (thread sampler) per block (fixes the tiling)")
     ap.add_argument("--lnf-final", type=float, default=None, help="override the workload's final ln f")
     ap.add_argument("--walkers-per-window", type=int, default=None,
                     help="override the workload's walkers per window (small cases for profiler captures)")
@@ -383,7 +387,10 @@ def run_gpu(args, w):
                                  precision=prec,
                                  sampler=smp)
     plain = args.form == "plain"
-    if not args.no_autotune and not plain:
+    if args.lanes is not None or args.wpb is not None:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, lanes_per_walker=args.lanes or 0, walkers_per_block=args.wpb or 0)
+    elif not args.no_autotune and not plain:
         from paper_1508_02748_gb300.autotune import autotune
         allowed = (P.SAMPLER_WARP, P.SAMPLER_THREAD) if args.sampler == "auto" else (smp,)
         cfg = autotune(cfg, device=str(dev), samplers=allowed)

@@ -52,11 +52,17 @@ extern "C" {
 #define REWL_E_JOIN (-7)        /* pieces cannot be joined (no common bins) */
 #define REWL_E_CAPACITY (-8)    /* output or workspace buffer too small */
 
-/* ln g arithmetic of the sampling tables. */
-#define REWL_FP64 0             /* double per bin */
-#define REWL_F32X2 1            /* compensated pair of floats (hi, lo) per bin */
-#define REWL_F32 2              /* one float per bin, plain accumulation: increments below half an
-                                   ulp of ln g are lost (precision-study demonstration; warp sampler) */
+/* ln g arithmetic of the sampling tables.  The exact formats keep, per bin,
+ * the value at the start of the current iteration (the base) and the
+ * iteration's visit count H; ln g = base + H ln f is formed exactly where it
+ * is needed, and the visits enter the base when the iteration ends.  With
+ * ln f = 2^-k (enforced: see lnf_init) every ln g is a dyadic rational, so
+ * both exact formats follow the sequential chain of Sec. 2 bit for bit. */
+#define REWL_FP64 0             /* base as a double per bin */
+#define REWL_F32X2 1            /* base as a compensated pair of floats (hi, lo) per bin */
+#define REWL_F32 2              /* ln g as one float per bin, rounded at every visit: increments
+                                   below half an ulp of ln g are lost (precision-study
+                                   demonstration; always runs on the thread sampler) */
 
 /* Sampling kernels (same trajectory, different mapping onto the GPU). */
 #define REWL_SAMPLER_WARP 0     /* 8/16/32 lanes per walker, 3/4/5 trials resolved per step */
@@ -87,9 +93,11 @@ typedef struct rewl_config {
     double overlap_M;
     int32_t walkers_per_window; /* independent walkers per window (Sec. 2), >= 1 */
     int32_t precision;          /* REWL_FP64, REWL_F32X2 or REWL_F32 */
-    double lnf_init;            /* ln f of the first iteration (> 0) */
+    double lnf_init;            /* ln f of the first iteration: a power of two >= 2^-60
+                                   (else REWL_E_INVALID; 1 in the workloads) */
     double lnf_final;           /* run ends after the first flat iteration with ln f <= this */
-    double lnf_factor;          /* ln f <- ln f * factor; 0.5 is f -> sqrt(f) (Sec. 2) */
+    double lnf_factor;          /* ln f <- ln f * factor, a power of two below 1; 0.5 is
+                                   f -> sqrt(f) (Sec. 2) */
     double flatness;            /* min H >= flatness * mean H (0.8, Sec. 3); six decimals */
     uint64_t exchange_interval; /* trials per walker between exchange sweeps (Sec. 2) */
     int32_t check_every;        /* cycles between flatness checks, >= 1 */
@@ -188,11 +196,14 @@ int rewl_get_windows(rewl_t *h, int32_t *host_out, size_t capacity);
 int rewl_get_walkers(rewl_t *h, int64_t *host_state, uint8_t *host_spins);
 
 /* Per-walker tables, walker-major, each window_bins = (e1-e0+1)(m1-m0+1)
- * entries in [e][m] order: ln g as double (converted from the compensated
- * pair for REWL_F32X2) and H as int32 (-1 = never visited).  Either pointer
- * may be NULL.  capacity counts entries per array. */
+ * entries in [e][m] order: ln g as double (exact formats: base + max(H, 0)
+ * ln f, formed in double) and H as int32 (-1 = never visited).  Either
+ * pointer may be NULL.  capacity counts entries per array. */
 int rewl_get_tables(rewl_t *h, double *host_lng, int32_t *host_H, size_t capacity);
-/* Overwrites the tables (tests set up join and flatness cases with it). */
+/* Overwrites the tables (tests set up join and flatness cases with it): the
+ * exact formats store base = ln g - max(H, 0) ln f with the current ln f
+ * (host_H NULL: the H on the device) and refresh the screens the sampler
+ * decides with.  count must equal the number of entries get returns. */
 int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t *host_H, size_t count);
 
 /* Final merge of each window's walkers, join (Eqs. 3-4, E then M) and
@@ -261,9 +272,10 @@ int rewl_batch_destroy(rewl_batch_t *b);
 
 /* Joined ln g(E,M) of tables already on the device, with no memory
  * allocated by the call.  The paper has no counterpart: this serves callers
- * that cannot allocate device memory (inside a region being captured into a
- * CUDA graph, under an external allocator that owns all device memory, or
- * with a fixed memory budget) but own their inputs and output.
+ * that may not call cudaMalloc -- a process whose device memory is all owned
+ * by an external allocator (a framework's caching pool), or one that fixes
+ * its memory budget up front -- but own their inputs and output.  The call
+ * synchronises on `stream` before it returns.
  *   cfg: the configuration the tables were sampled with (geometry, walkers).
  *   d_lng, d_H: device pointers, n_walkers x window_bins entries each,
  *     walker-major, [e][m] within a walker (the layout rewl_get_tables
@@ -279,7 +291,8 @@ int rewl_batch_destroy(rewl_batch_t *b);
  * current: make it before any stream capture.  All calls share the array and
  * it keeps the last call's contents; calls that overlap on the GPU race and
  * must be serialised by the caller.  Errors: REWL_E_INVALID, REWL_E_CAPACITY,
- * REWL_E_JOIN, REWL_E_CUDA; rewl_noalloc_last_error() gives the message. */
+ * REWL_E_JOIN, REWL_E_CUDA; rewl_noalloc_last_error() gives the calling
+ * thread's last message. */
 int rewl_join_noalloc(const rewl_config *cfg, const double *d_lng, const int32_t *d_H, double *d_out,
                       void *stream);
 const char *rewl_noalloc_last_error(void);

@@ -111,8 +111,16 @@ bool bin_can_hold(int L, int e, int m)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// x = 2^k for an integer k (x finite and positive)
+bool is_pow2(double x)
+{
+    if (!(x > 0.0) || !std::isfinite(x)) return false;
+    int ex = 0;
+    return std::frexp(x, &ex) == 0.5;
+}
+
 struct Layout {
-    size_t st, rect, active, spins, we, wm, wt, wflat, lng, H;
+    size_t st, rect, active, spins, we, wm, wt, wflat, lng, H, scr;
     size_t piece, off, GE, eshift, efrom, eto, ematch, rowok, F, mshift, mfrom, mto, mmatch, J, red, marg, gbuf;
     size_t eslice, mslice;
     size_t jk_ref, jk_sum, jk_sq, jk_mean, jk_err;
@@ -130,6 +138,10 @@ int check_config(const rewl_config *c, const char **why)
     if (c->walkers_per_window < 1 || c->walkers_per_window > 1024) { *why = "walkers_per_window must be in [1, 1024]"; return REWL_E_INVALID; }
     if (c->precision != REWL_FP64 && c->precision != REWL_F32X2 && c->precision != REWL_F32) { *why = "unknown precision"; return REWL_E_INVALID; }
     if (!(c->lnf_init > 0.0 && c->lnf_final > 0.0 && c->lnf_factor > 0.0 && c->lnf_factor < 1.0)) { *why = "bad ln f schedule"; return REWL_E_INVALID; }
+    if (!is_pow2(c->lnf_init) || !is_pow2(c->lnf_factor) || c->lnf_init < 0x1p-60) {
+        *why = "lnf_init and lnf_factor must be powers of two (ln f = 2^-k keeps every ln g exact), lnf_init >= 2^-60";
+        return REWL_E_INVALID;
+    }
     if (!(c->flatness > 0.0 && c->flatness <= 1.0)) { *why = "flatness must be in (0, 1]"; return REWL_E_INVALID; }
     if (c->exchange_interval < 1) { *why = "exchange_interval must be >= 1"; return REWL_E_INVALID; }
     if (c->check_every < 1) { *why = "check_every must be >= 1"; return REWL_E_INVALID; }
@@ -143,6 +155,7 @@ int check_config(const rewl_config *c, const char **why)
 Dims dims_of(const rewl_config *c)
 {
     Dims d;
+    d.precision = c->precision;
     d.L = c->L; d.N = c->L * c->L;
     d.wpr = (c->L + 31) / 32;
     d.nwords = d.L * d.wpr;
@@ -178,6 +191,7 @@ Layout layout_of(const Dims &d)
     L.wflat = take(sizeof(int32_t) * d.nwalk);
     L.lng = take(8 * (size_t)d.nwalk * d.tstride);
     L.H = take(4 * (size_t)d.nwalk * d.tstride);
+    L.scr = take(d.precision == REWL_F32 ? 0 : 4 * (size_t)d.nwalk * d.tstride);
     L.piece = take(8 * (size_t)d.nwin * d.tstride);
     L.off = take(8 * (size_t)d.nwalk);
     L.GE = take(8 * (size_t)d.nwin * d.wE);
@@ -265,7 +279,7 @@ cudaError_t queue_cycle(rewl_t *h, bool check)
     if ((e = launch_exchange(h->p, h->max_pairs, h->stream)) != cudaSuccess) return e;
     if (check && (e = launch_flat(h->p, h->stream)) != cudaSuccess) return e;
     if ((e = launch_decide(h->p, DECIDE_XSTEP | DECIDE_CYCLE | (check ? DECIDE_CHECK : 0), h->stream)) != cudaSuccess) return e;
-    if (check && (e = launch_reset(h->p, h->stream)) != cudaSuccess) return e;
+    if (check && (e = launch_fold(h->p, 1, h->stream)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -375,6 +389,7 @@ int create_impl(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_
     p.lng2 = (float2 *)(base + lay.lng);
     p.lng1 = (float *)(base + lay.lng);
     p.H = (int32_t *)(base + lay.H);
+    p.scr = (float *)(base + lay.scr);
     p.st = (DevState *)(base + lay.st);
     JoinScratch &j = h->j;
     j.piece = (double *)(base + lay.piece);
@@ -453,6 +468,7 @@ int create_impl(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_
     // Tables: ln g = 0, H = -1 (never visited).
     CKB(cudaMemsetAsync(p.lng, 0, 8 * (size_t)d.nwalk * d.tstride, h->stream));
     CKB(cudaMemsetAsync(p.H, 0xFF, 4 * (size_t)d.nwalk * d.tstride, h->stream));
+    if (p.precision != REWL_F32) CKB(cudaMemsetAsync(p.scr, 0, 4 * (size_t)d.nwalk * d.tstride, h->stream));
     CKB(cudaMemsetAsync(h->d_fail, 0, 4, h->stream));
     if (!initialise) {
         CKB(cudaStreamSynchronize(h->stream));
@@ -491,7 +507,7 @@ extern "C" int rewl_create(const rewl_config *cfg, const uint8_t *host_init_spin
 
 namespace {
 
-const char kCkptMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '1'};
+const char kCkptMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '2'};
 
 struct CkptFile {
     FILE *f = nullptr;
@@ -549,7 +565,7 @@ extern "C" int rewl_save(rewl_t *h, const char *path)
     CkptFile cf;
     cf.f = fopen(path, "wb");
     if (!cf.f) return fail(h, REWL_E_INVALID, "cannot open %s for writing", path);
-    const uint32_t version = 1, csize = (uint32_t)sizeof(rewl_config);
+    const uint32_t version = 2, csize = (uint32_t)sizeof(rewl_config);
     const unsigned long long hc = h->host_cycle;
     if (fwrite(kCkptMagic, 1, 8, cf.f) != 8 || fwrite(&version, 4, 1, cf.f) != 1 || fwrite(&csize, 4, 1, cf.f) != 1 ||
         fwrite(&h->cfg, sizeof(rewl_config), 1, cf.f) != 1 || fwrite(&hc, 8, 1, cf.f) != 1)
@@ -571,7 +587,7 @@ extern "C" int rewl_checkpoint_config(const char *path, rewl_config *cfg)
     char magic[8];
     uint32_t version = 0, csize = 0;
     if (fread(magic, 1, 8, cf.f) != 8 || std::memcmp(magic, kCkptMagic, 8) != 0 || fread(&version, 4, 1, cf.f) != 1 ||
-        fread(&csize, 4, 1, cf.f) != 1 || version != 1 || csize != sizeof(rewl_config) ||
+        fread(&csize, 4, 1, cf.f) != 1 || version != 2 || csize != sizeof(rewl_config) ||
         fread(cfg, sizeof(rewl_config), 1, cf.f) != 1)
         return fail(nullptr, REWL_E_INVALID, "%s is not a librewl checkpoint of this version", path);
     return REWL_OK;
@@ -600,6 +616,12 @@ extern "C" int rewl_load(const char *path, void *d_workspace, size_t workspace_b
             rewl_destroy(h);
             return rc;
         }
+    }
+    // the screens are derived from the restored tables
+    if (launch_fold(h->p, 0, h->stream) != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        fail(nullptr, REWL_E_CUDA, "screen refresh after restore failed");
+        rewl_destroy(h);
+        return REWL_E_CUDA;
     }
     h->host_cycle = hc;
     *out = h;
@@ -659,7 +681,7 @@ extern "C" int rewl_enqueue_cycle(rewl_t *h, int parts)
         CK(h, launch_exchange(h->p, h->max_pairs, h->stream));
         if (check) CK(h, launch_flat(h->p, h->stream));
         CK(h, launch_decide(h->p, DECIDE_XSTEP | DECIDE_CYCLE | (check ? DECIDE_CHECK : 0), h->stream));
-        if (check) CK(h, launch_reset(h->p, h->stream));
+        if (check) CK(h, launch_fold(h->p, 1, h->stream));
         h->host_cycle += 1;
     }
     return REWL_OK;
@@ -725,7 +747,7 @@ extern "C" int rewl_check(rewl_t *h, int32_t *all_flat)
     if (!h) return REWL_E_INVALID;
     CK(h, launch_flat(h->p, h->stream));
     CK(h, launch_decide(h->p, DECIDE_CHECK, h->stream));
-    CK(h, launch_reset(h->p, h->stream));
+    CK(h, launch_fold(h->p, 1, h->stream));
     DevState ds;
     int rc = read_state(h, &ds);
     if (rc) return rc;
@@ -792,16 +814,27 @@ extern "C" int rewl_get_walkers(rewl_t *h, int64_t *host_state, uint8_t *host_sp
     return REWL_OK;
 }
 
+// Host copies of the tables.  Exact formats store base and H; the value
+// handed out is ln g = base + max(H, 0) ln f, the sum formed in double (exact
+// for the dyadic schedule), and rewl_set_tables stores base = ln g -
+// max(H, 0) ln f and refreshes the screens on the device.
 extern "C" int rewl_get_tables(rewl_t *h, double *host_lng, int32_t *host_H, size_t capacity)
 {
     if (!h) return REWL_E_INVALID;
     const Params &p = h->p;
     const size_t n = (size_t)p.nwalk * p.T;
     if (capacity < n) return fail(h, REWL_E_CAPACITY, "need %zu entries", n);
+    DevState ds;
+    int rc = read_state(h, &ds);
+    if (rc && rc != REWL_E_OVERFLOW) return rc;
+    std::vector<int32_t> Hv(n);
+    CK(h, cudaMemcpy2DAsync(Hv.data(), 4 * (size_t)p.T, p.H, 4 * (size_t)p.tstride, 4 * (size_t)p.T, p.nwalk,
+                            cudaMemcpyDeviceToHost, h->stream));
     if (host_lng) {
         if (p.precision == REWL_FP64) {
             CK(h, cudaMemcpy2DAsync(host_lng, 8 * (size_t)p.T, p.lng, 8 * (size_t)p.tstride, 8 * (size_t)p.T,
                                     p.nwalk, cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
         } else if (p.precision == REWL_F32X2) {
             std::vector<float2> tmp(n);
             CK(h, cudaMemcpy2DAsync(tmp.data(), 8 * (size_t)p.T, p.lng2, 8 * (size_t)p.tstride, 8 * (size_t)p.T,
@@ -815,11 +848,13 @@ extern "C" int rewl_get_tables(rewl_t *h, double *host_lng, int32_t *host_H, siz
             CK(h, cudaStreamSynchronize(h->stream));
             for (size_t i = 0; i < n; ++i) host_lng[i] = (double)tmp[i];
         }
+        if (p.precision != REWL_F32)
+            for (size_t i = 0; i < n; ++i)
+                if (Hv[i] > 0) host_lng[i] += (double)Hv[i] * ds.lnf;
     }
-    if (host_H)
-        CK(h, cudaMemcpy2DAsync(host_H, 4 * (size_t)p.T, p.H, 4 * (size_t)p.tstride, 4 * (size_t)p.T, p.nwalk,
-                                cudaMemcpyDeviceToHost, h->stream));
-    return sync(h);
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (host_H) std::memcpy(host_H, Hv.data(), 4 * n);
+    return REWL_OK;
 }
 
 extern "C" int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t *host_H, size_t count)
@@ -828,22 +863,38 @@ extern "C" int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t 
     const Params &p = h->p;
     const size_t n = (size_t)p.nwalk * p.T;
     if (count != n) return fail(h, REWL_E_CAPACITY, "need exactly %zu entries", n);
+    DevState ds;
+    int rc = read_state(h, &ds);
+    if (rc && rc != REWL_E_OVERFLOW) return rc;
+    std::vector<int32_t> Hv(n);
+    if (host_H) {
+        std::memcpy(Hv.data(), host_H, 4 * n);
+    } else {
+        CK(h, cudaMemcpy2DAsync(Hv.data(), 4 * (size_t)p.T, p.H, 4 * (size_t)p.tstride, 4 * (size_t)p.T, p.nwalk,
+                                cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
     if (host_lng) {
+        std::vector<double> base(host_lng, host_lng + n);
+        if (p.precision != REWL_F32)
+            for (size_t i = 0; i < n; ++i)
+                if (Hv[i] > 0) base[i] -= (double)Hv[i] * ds.lnf;
         if (p.precision == REWL_FP64) {
-            CK(h, cudaMemcpy2DAsync(p.lng, 8 * (size_t)p.tstride, host_lng, 8 * (size_t)p.T, 8 * (size_t)p.T,
+            CK(h, cudaMemcpy2DAsync(p.lng, 8 * (size_t)p.tstride, base.data(), 8 * (size_t)p.T, 8 * (size_t)p.T,
                                     p.nwalk, cudaMemcpyHostToDevice, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
         } else if (p.precision == REWL_F32X2) {
             std::vector<float2> tmp(n);
             for (size_t i = 0; i < n; ++i) {
-                const float hi = (float)host_lng[i];
-                tmp[i] = make_float2(hi, (float)(host_lng[i] - (double)hi));
+                const float hi = (float)base[i];
+                tmp[i] = make_float2(hi, (float)(base[i] - (double)hi));
             }
             CK(h, cudaMemcpy2DAsync(p.lng2, 8 * (size_t)p.tstride, tmp.data(), 8 * (size_t)p.T, 8 * (size_t)p.T,
                                     p.nwalk, cudaMemcpyHostToDevice, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
         } else {
             std::vector<float> tmp(n);
-            for (size_t i = 0; i < n; ++i) tmp[i] = (float)host_lng[i];
+            for (size_t i = 0; i < n; ++i) tmp[i] = (float)base[i];
             CK(h, cudaMemcpy2DAsync(p.lng1, 4 * (size_t)p.tstride, tmp.data(), 4 * (size_t)p.T, 4 * (size_t)p.T,
                                     p.nwalk, cudaMemcpyHostToDevice, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
@@ -852,6 +903,7 @@ extern "C" int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t 
     if (host_H)
         CK(h, cudaMemcpy2DAsync(p.H, 4 * (size_t)p.tstride, host_H, 4 * (size_t)p.T, 4 * (size_t)p.T, p.nwalk,
                                 cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_fold(p, 0, h->stream));
     return sync(h);
 }
 

@@ -41,6 +41,7 @@ enum : uint32_t { TAG_INIT = 1, TAG_DRIVE = 2, TAG_TRIAL = 3, TAG_PERM = 4, TAG_
 // Scalars of a run that live in device memory (part of the workspace).
 struct DevState {
     double lnf;                       // ln f of the current iteration
+    double lnf_done;                  // ln f of the iteration that ended at the last advance
     unsigned long long cycle;         // cycles run
     unsigned long long xstep;         // exchange sweeps run (phase = xstep mod 4)
     unsigned long long exch_attempts;
@@ -89,10 +90,20 @@ struct Params {
     int32_t *we, *wm; // bins of each walker's configuration
     unsigned long long *wt;  // trials done per walker
     int32_t *wflat;   // last flatness verdict
-    double *lng;      // REWL_FP64: nwalk x tstride
-    float2 *lng2;     // REWL_F32X2: nwalk x tstride (hi, lo)
-    float *lng1;      // REWL_F32: nwalk x tstride
-    int32_t *H;       // nwalk x tstride, -1 = never visited
+    // Tables, nwalk x tstride entries each.  Exact formats (REWL_FP64,
+    // REWL_F32X2) hold ln g(b) = base(b) + max(H(b), 0) * ln f: `lng`/`lng2`
+    // is the base, the value at the start of the current iteration, and H
+    // counts the iteration's visits, so a visit changes H only; the base takes
+    // the visits in once per iteration (k_fold).  With ln f = 2^-k the sum is
+    // exact and equals the sequential additions of Sec. 2.  REWL_F32 holds
+    // ln g itself in `lng1`, rounded at every visit.
+    double *lng;      // REWL_FP64 base
+    float2 *lng2;     // REWL_F32X2 base (hi, lo)
+    float *lng1;      // REWL_F32 ln g
+    int32_t *H;       // -1 = never visited
+    float *scr;       // exact formats: float screen of the base, base(b) - c_w rounded to
+                      //   nearest, c_w a per-walker constant (the walker's ln g at the last
+                      //   fold); the decisions screen differences of these values
     DevState *st;
 };
 
@@ -129,12 +140,13 @@ size_t tree_smem_per_warp(const Params &p, bool smt);
 cudaError_t launch_exchange(const Params &p, int max_pairs, cudaStream_t s);
 cudaError_t launch_flat(const Params &p, cudaStream_t s);
 cudaError_t launch_decide(const Params &p, int flags, cudaStream_t s);
-cudaError_t launch_reset(const Params &p, cudaStream_t s);
+// Iteration advance (fold = 1, only when the last check ended an iteration):
+// base += H * lnf_done and H -> 0 on visited bins; the screens are refreshed
+// in both cases (fold = 0: after the tables were written from the host).
+cudaError_t launch_fold(const Params &p, int fold, cudaStream_t s);
 cudaError_t launch_rel_diff(const double *a, const double *b, double *out, size_t n, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *d_ctr, uint32_t k0, uint32_t k1, uint32_t *d_out,
                           uint64_t n, cudaStream_t s);
-cudaError_t launch_tables_to_double(const Params &p, double *d_out, cudaStream_t s);
-cudaError_t launch_tables_from_double(const Params &p, const double *d_in, cudaStream_t s);
 cudaError_t launch_join(const Params &p, const JoinScratch &j, cudaStream_t s);
 cudaError_t launch_marginal_e(const Params &p, const JoinScratch &j, cudaStream_t s);
 cudaError_t launch_jk_accum(const JoinScratch &j, const double *x, size_t n, int k, cudaStream_t s);
@@ -144,10 +156,12 @@ enum : int { DECIDE_XSTEP = 1, DECIDE_CYCLE = 2, DECIDE_CHECK = 4 };
 
 // Host-side geometry and configuration helpers (rewl_api.cu).
 struct Dims {
+    int precision;
     int L, N, wpr, nwords, nE, nM, W, nwin, nwalk, wE, wM, T;
     long long tstride;
 };
 void axis_windows(int bins, int n, double overlap, std::vector<int> &lo, std::vector<int> &hi);
+bool is_pow2(double x);
 bool bin_can_hold(int L, int e, int m);
 int check_config(const rewl_config *c, const char **why);
 Dims dims_of(const rewl_config *c);

@@ -25,12 +25,19 @@ namespace rewl {
 
 namespace {
 
+// ln g of table entry i: base + max(H, 0) ln f in the exact formats (a
+// caller's plain table is read with ln f = 0), the stored value for REWL_F32.
 __device__ __forceinline__ double lng_at(const Params &p, size_t i)
 {
-    if (p.precision == REWL_FP64) return p.lng[i];
     if (p.precision == REWL_F32) return (double)p.lng1[i];
-    const float2 v = p.lng2[i];
-    return (double)v.x + (double)v.y;
+    double b;
+    if (p.precision == REWL_FP64) {
+        b = p.lng[i];
+    } else {
+        const float2 v = p.lng2[i];
+        b = (double)v.x + (double)v.y;
+    }
+    return fma((double)max(p.H[i], 0), p.st->lnf, b);
 }
 
 __device__ __forceinline__ bool all_seen(const Params &p, int win, int bin)

@@ -32,13 +32,13 @@ __device__ __forceinline__ uint32_t sbit(const uint32_t *sm, int nb, int r, int 
     return (sm[(r * WPR + q) * nb] >> (c & 31)) & 1u;
 }
 
-// ln g access for the two table precisions.
-__device__ __forceinline__ double lng_read(const Params &p, size_t i)
+// ln g of table entry i: base + max(H, 0) ln f in the exact formats (exact
+// in double for the dyadic schedule), the stored value for REWL_F32.
+__device__ __forceinline__ double lng_read(const Params &p, size_t i, double lnf)
 {
-    if (p.precision == REWL_FP64) return p.lng[i];
     if (p.precision == REWL_F32) return (double)p.lng1[i];
-    const float2 v = p.lng2[i];
-    return (double)v.x + (double)v.y;
+    const double b = p.precision == REWL_FP64 ? p.lng[i] : Tab<REWL_F32X2>::exact(p.lng2[i]);
+    return fma((double)max(p.H[i], 0), lnf, b);
 }
 
 }  // namespace
@@ -153,7 +153,8 @@ cudaError_t launch_drive(const Params &p, int32_t *d_fail, cudaStream_t s)
 // -------------------------------------------------------------- sweep ----
 
 // ntrials Wang-Landau trials per walker, one thread per walker (the sampler
-// for runs with many walkers, where the walkers alone fill the GPU).
+// for runs with many walkers, where the walkers alone fill the GPU, the plain
+// one-walker-per-launch form, and plain-float tables).
 //
 // Trial t: site and u from the TRIAL stream; flipping spin s with n_up up
 // neighbours moves the bins by de = s (n_up - 2), dm = -s (s = +-1).  A
@@ -162,21 +163,20 @@ cudaError_t launch_drive(const Params &p, int32_t *d_fail, cudaStream_t s)
 // ln u < delta (Eq. 1 in logarithms).  Then ln g(cur) += ln f and
 // H(cur) += 1 for the bin the walker is in (Sec. 2).
 //
-// The walker's own bin is kept in registers: its table value when entered
-// and the visits since; ln g(cur) = value + visits * ln f is formed exactly
-// (fma in double, a compensated float pair for REWL_F32X2) -- the same number
-// as the sequential additions whenever ln f = 2^-k -- and written back when
-// the walker leaves the bin and at the end (a bin left by the very first
-// trial of a launch keeps its entries, H = -1 included).  The bin proposed
-// is never the current one (dm != 0), so its table entry is up to date.
-//
-// The decision is screened in float: c = ln g(cur), b = ln g(new) and ln u
-// are each known to within a few float roundings (|error| < 2^-21 of their
-// sum of magnitudes), so when ln u lies farther than
-//     M = 2^-20 (|c| + |b| + |c_0| + |ln u|) + 2^-20
-// from c - b the float comparison gives the exact answer; otherwise delta and
-// ln u are evaluated in double.  REWL_F32 (plain float, a precision
-// demonstration) compares the rounded float values directly.
+// Exact formats: ln g(b) = base(b) + max(H(b), 0) ln f with the base fixed
+// during the iteration, so a visit is H + 1 alone.  The walker's own count is
+// kept in a register and written back when it leaves the bin and at the end
+// (a bin left by the very first trial of a launch keeps its H, -1 included).
+// The proposed bin is never the current one (dm != 0), so its H is up to
+// date.  The decision is screened in float from the screens S (base minus a
+// per-walker constant, rounded): with c = S_c + n_c ln f and b = S_b + n_b
+// ln f in float, when ln u lies farther than
+//     M = 2^-20 (|c| + |b| + |S_c| + |S_b| + |ln u|) + 2^-20
+// from c - b the float comparison gives the exact answer (the error bound is
+// that of the tree sampler); otherwise delta and ln u are evaluated in
+// double.  REWL_F32 (plain float, a precision demonstration) keeps ln g
+// itself, adds ln f with a float rounding at every visit and compares the
+// rounded values directly.
 //
 // REG: the lattice (N <= 64, bit i*L + j) is one 64-bit register; otherwise
 // it lives in shared memory, word q of row r of thread t at
@@ -186,11 +186,10 @@ __global__ void __launch_bounds__(128) k_sweep_thread(Params p, unsigned long lo
 {
     using TB = Tab<PREC>;
     using Elem = typename TB::Elem;
-    using Val = typename TB::Val;
     extern __shared__ uint32_t sm_all[];
     const int nb = blockDim.x, tid = threadIdx.x;
     const int w = p.walker0 + blockIdx.x * nb + tid;
-    if (w >= p.nwalk) return;
+    if (w >= p.nwalk || ntrials == 0) return;
     if (!p.active[w / p.W] || p.st->done) return;
     uint32_t *sm = sm_all + tid;
     const int L = p.L, nwords = L * WPR;
@@ -204,21 +203,31 @@ __global__ void __launch_bounds__(128) k_sweep_thread(Params p, unsigned long lo
     const int4 R = p.rect[w / p.W];
     const int wM = p.wM;
     const unsigned spanE = (unsigned)(R.y - R.x), spanM = (unsigned)(R.w - R.z);
-    Elem *tl = ((PREC == REWL_FP64) ? reinterpret_cast<Elem *>(p.lng)
-              : (PREC == REWL_F32X2) ? reinterpret_cast<Elem *>(p.lng2) : reinterpret_cast<Elem *>(p.lng1))
-             + (size_t)w * p.tstride;
+    const Elem *gb = reinterpret_cast<const Elem *>(PREC == REWL_FP64 ? (const void *)p.lng
+                                                  : PREC == REWL_F32X2 ? (const void *)p.lng2 : (const void *)p.lng1)
+                   + (size_t)w * p.tstride;
+    float *t1 = p.lng1 + (size_t)w * p.tstride;      // REWL_F32 values
+    const float *S = p.scr + (size_t)w * p.tstride;  // exact formats
     int32_t *tH = p.H + (size_t)w * p.tstride;
     const double lnf = p.st->lnf;
-    const float lnf32 = trunc_f(lnf);
+    const float lnf32 = __double2float_rn(lnf);
     const uint32_t N = (uint32_t)p.N;
 
     int e = p.we[w], m = p.wm[w];
     int ci = (e - R.x) * wM + (m - R.z);
-    Val lbase = TB::load(tl, ci);
-    float base32 = TB::approx(lbase);
-    int lq = 0;          // ln f steps since lbase
-    int hq = 0;          // visits not yet in H
-    int hbase = tH[ci];
+    int lq;              // exact formats: H of the current bin; REWL_F32: visits since v1
+    int hq = 0;          // visits not yet written to H
+    int hbase = tH[ci];  // REWL_F32: H of the current bin when entered
+    float base32;        // exact formats: screen of the current bin
+    float v1 = 0.0f;     // REWL_F32: value of the current bin when entered
+    if (PREC == REWL_F32) {
+        lq = 0;
+        v1 = t1[ci];
+        base32 = v1;
+    } else {
+        lq = max(hbase, 0);
+        base32 = S[ci];
+    }
     unsigned long long t = p.wt[w];
     const unsigned long long tend = t + ntrials;
     int err = 0;
@@ -227,6 +236,17 @@ __global__ void __launch_bounds__(128) k_sweep_thread(Params p, unsigned long lo
         if (REG) return (uint32_t)(lat >> (r * L + c)) & 1u;
         const int q = (WPR == 1) ? 0 : (c >> 5);
         return (sm[(r * WPR + q) * nb] >> (c & 31)) & 1u;
+    };
+    auto flush = [&]() {
+        if (PREC == REWL_F32) {
+            const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
+            if (hv > 0x7FFFFFFFll) err = 1;
+            t1[ci] = f32_visits(v1, lq, lnf32);
+            tH[ci] = (int32_t)hv;
+        } else {
+            tH[ci] = lq;
+            err |= lq < 0;
+        }
     };
 
     u32x4 x = philox10((uint32_t)(t >> 1), (uint32_t)(t >> 33), (uint32_t)w, TAG_TRIAL, p.key0, p.key1);
@@ -246,54 +266,53 @@ __global__ void __launch_bounds__(128) k_sweep_thread(Params p, unsigned long lo
         const int mn = m + (sp ? -1 : 1);
         if ((unsigned)(en - R.x) <= spanE && (unsigned)(mn - R.z) <= spanM) {
             const int ni = (en - R.x) * wM + (mn - R.z);
-            const Val tn = TB::load(tl, ni);
-            const float nb32 = TB::approx(tn);
             bool acc;
+            int hn = 0;
+            float vn = 0.0f;
             if constexpr (PREC == REWL_F32) {
-                acc = lnu < TB::add(lbase, lq, lnf, lnf32) - tn;
+                vn = t1[ni];
+                acc = lnu < f32_visits(v1, lq, lnf32) - vn;
             } else {
-                const float c32 = __fmaf_rn((float)lq, lnf32, base32);
-                const float d32 = c32 - nb32;
-                const float M = (fabsf(c32) + fabsf(nb32) + fabsf(base32) + fabsf(lnu)) * 0x1p-20f + 0x1p-20f;
+                hn = max(tH[ni], 0);
+                vn = S[ni];
+                const float c32 = __fmaf_rn(__int2float_rn(lq), lnf32, base32);
+                const float n32 = __fmaf_rn(__int2float_rn(hn), lnf32, vn);
+                const float d32 = __fsub_rn(c32, n32);
+                const float M = __fmaf_rn(fabsf(c32) + fabsf(n32) + fabsf(base32) + fabsf(vn) + fabsf(lnu),
+                                          0x1p-20f, 0x1p-20f);
                 if (lnu < d32 - M) {
                     acc = true;
                 } else if (lnu > d32 + M) {
                     acc = false;
                 } else {
-                    const double delta = fma((double)lq, lnf, TB::exact(lbase)) - TB::exact(tn);
+                    const double delta = fma((double)lq, lnf, TB::exact(gb[ci])) - fma((double)hn, lnf, TB::exact(gb[ni]));
                     acc = delta >= 0.0 || log(unit_open_d(xu)) < delta;
                 }
             }
             if (acc) {
                 if (REG) lat ^= 1ull << (i * L + j);
                 else sm[(i * WPR + ((WPR == 1) ? 0 : (j >> 5))) * nb] ^= 1u << (j & 31);
-                if (hq) {
-                    const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
-                    if (hv > 0x7FFFFFFFll) err = 1;
-                    tl[ci] = TB::add(lbase, lq, lnf, lnf32);
-                    tH[ci] = (int32_t)hv;
+                if (hq) flush();
+                ci = ni; hq = 0;
+                if (PREC == REWL_F32) {
+                    v1 = vn; lq = 0; hbase = tH[ni];
+                } else {
+                    lq = hn; base32 = vn;
                 }
-                ci = ni; lbase = tn; base32 = nb32; lq = 0; hq = 0; hbase = tH[ni];
                 e = en; m = mn;
             }
         }
         ++lq;
         ++hq;
-        if (lq == (1 << 22)) {              // keep the float screen's counts exact
-            lbase = TB::add(lbase, lq, lnf, lnf32);
-            base32 = TB::approx(lbase);
+        if (PREC == REWL_F32 && lq == 64) {   // keep the per-visit roundings short
+            v1 = f32_visits(v1, lq, lnf32);
             lq = 0;
         }
         ++t;
         if (!(t & 1ull))
             x = philox10((uint32_t)(t >> 1), (uint32_t)(t >> 33), (uint32_t)w, TAG_TRIAL, p.key0, p.key1);
     }
-    if (hq) {
-        const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
-        if (hv > 0x7FFFFFFFll) err = 1;
-        tl[ci] = TB::add(lbase, lq, lnf, lnf32);
-        tH[ci] = (int32_t)hv;
-    }
+    if (hq) flush();
     p.we[w] = e;
     p.wm[w] = m;
     p.wt[w] = t;
@@ -335,10 +354,10 @@ cudaError_t launch_thread(const Params &p, int blocks, int wpb, uint64_t ntrials
 
 cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int wpb, cudaStream_t s)
 {
-    if (p.sampler == REWL_SAMPLER_WARP) {
-        // staged exact tables fold their visit counts once per launch: fewer
-        // than 2^22 trials per launch keep every count exact in float
-        const uint64_t chunk = (p.smt && p.precision != REWL_F32) ? (1ull << 22) : (1ull << 30);
+    // the tree sampler serves the exact table formats; plain-float tables
+    // (a precision demonstration) always run on the thread sampler
+    if (p.sampler == REWL_SAMPLER_WARP && p.precision != REWL_F32) {
+        const uint64_t chunk = 1ull << 30;
         while (ntrials > 0) {
             const uint64_t n = ntrials > chunk ? chunk : ntrials;
             const cudaError_t e = launch_sweep_tree(p, n, p.group, wpb, p.smt != 0, s);
@@ -347,7 +366,7 @@ cudaError_t launch_sweep(const Params &p, uint64_t ntrials, int wpb, cudaStream_
         }
         return cudaSuccess;
     }
-    if (wpb <= 0) wpb = 32;
+    if (p.sampler == REWL_SAMPLER_WARP || wpb <= 0) wpb = 32;
     return launch_thread(p, (p.nwalk + wpb - 1) / wpb, wpb, ntrials, s);
 }
 
@@ -405,10 +424,11 @@ __global__ void k_exchange(Params p)
         const bool yinA = eY >= RA.x && eY <= RA.y && mY >= RA.z && mY <= RA.w;
         if (!xinB || !yinA) continue;
         const size_t bi = (size_t)wi * p.tstride, bj = (size_t)wj * p.tstride;
-        const double giX = lng_read(p, bi + (size_t)(eX - RA.x) * p.wM + (mX - RA.z));
-        const double giY = lng_read(p, bi + (size_t)(eY - RA.x) * p.wM + (mY - RA.z));
-        const double gjY = lng_read(p, bj + (size_t)(eY - RB.x) * p.wM + (mY - RB.z));
-        const double gjX = lng_read(p, bj + (size_t)(eX - RB.x) * p.wM + (mX - RB.z));
+        const double lnf = p.st->lnf;
+        const double giX = lng_read(p, bi + (size_t)(eX - RA.x) * p.wM + (mX - RA.z), lnf);
+        const double giY = lng_read(p, bi + (size_t)(eY - RA.x) * p.wM + (mY - RA.z), lnf);
+        const double gjY = lng_read(p, bj + (size_t)(eY - RB.x) * p.wM + (mY - RB.z), lnf);
+        const double gjX = lng_read(p, bj + (size_t)(eX - RB.x) * p.wM + (mX - RB.z), lnf);
         const double lnP = (giX - giY) + (gjY - gjX);
         const u32x4 r = philox10((uint32_t)xs, pair, (uint32_t)k, TAG_EXCH, p.key0, p.key1);
         atomicAdd(&s_att, 1ull);
@@ -510,6 +530,7 @@ __global__ void k_decide(Params p, int flags)
         if (nf == p.n_active_walkers) {
             st->advanced = 1;
             st->iter += 1;
+            st->lnf_done = st->lnf;
             if (st->lnf <= p.lnf_final) st->done = 1;
             else st->lnf = st->lnf * p.lnf_factor;
         }
@@ -522,26 +543,64 @@ cudaError_t launch_decide(const Params &p, int flags, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// H reset after an iteration ends: visited bins back to 0, unvisited stay -1.
-__global__ void k_reset(Params p)
+// Iteration advance (f -> sqrt f, Sec. 2), one block per walker.  Exact
+// formats: the finished iteration's visits enter the base, base += H ln f
+// (ln f of that iteration; exact for the dyadic schedule), and H goes back to
+// 0 on visited bins (-1, never visited, stays).  The screens are refreshed:
+// S = base - c_w rounded to float, c_w = ln g of the walker's current bin.
+// REWL_F32: H reset only.  fold = 0 refreshes the screens alone (after the
+// tables were written from the host); fold = 1 does nothing unless the last
+// check ended an iteration.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_fold(Params p, int fold)
 {
-    if (!p.st->advanced) return;
-    const size_t n = (size_t)p.nwalk * p.tstride / 4;
-    int4 *H4 = reinterpret_cast<int4 *>(p.H);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        int4 v = H4[i];
-        v.x = v.x > 0 ? 0 : v.x; v.y = v.y > 0 ? 0 : v.y;
-        v.z = v.z > 0 ? 0 : v.z; v.w = v.w > 0 ? 0 : v.w;
-        H4[i] = v;
+    using TB = Tab<PREC>;
+    using Elem = typename TB::Elem;
+    if (fold && !p.st->advanced) return;
+    const int w = blockIdx.x;
+    int32_t *H = p.H + (size_t)w * p.tstride;
+    const int T = p.T;
+    if (PREC == REWL_F32) {
+        if (fold)
+            for (int k = threadIdx.x; k < T; k += blockDim.x) H[k] = H[k] > 0 ? 0 : H[k];
+        return;
+    }
+    Elem *B = reinterpret_cast<Elem *>(PREC == REWL_FP64 ? (void *)p.lng : (void *)p.lng2) + (size_t)w * p.tstride;
+    float *S = p.scr + (size_t)w * p.tstride;
+    const double lnf = fold ? p.st->lnf_done : p.st->lnf;
+    __shared__ double s_c;
+    if (threadIdx.x == 0) {
+        const int4 R = p.rect[w / p.W];
+        const int e = p.we[w], m = p.wm[w];
+        double c = 0.0;
+        if (p.active[w / p.W] && e >= R.x && e <= R.y && m >= R.z && m <= R.w) {
+            const int ci = (e - R.x) * p.wM + (m - R.z);
+            c = fma((double)max(H[ci], 0), lnf, TB::exact(B[ci]));
+        }
+        s_c = c;
+    }
+    __syncthreads();
+    const double c = s_c;
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+        double v = TB::exact(B[k]);
+        if (fold) {
+            const int h = H[k];
+            if (h > 0) {
+                v = fma((double)h, lnf, v);
+                B[k] = TB::from(v);
+                H[k] = 0;
+            }
+        }
+        S[k] = __double2float_rn(v - c);
     }
 }
 
-cudaError_t launch_reset(const Params &p, cudaStream_t s)
+cudaError_t launch_fold(const Params &p, int fold, cudaStream_t s)
 {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_reset<<<sms * 4, 256, 0, s>>>(p);
+    if (p.nwalk <= 0) return cudaSuccess;
+    if (p.precision == REWL_FP64) k_fold<REWL_FP64><<<p.nwalk, 256, 0, s>>>(p, fold);
+    else if (p.precision == REWL_F32X2) k_fold<REWL_F32X2><<<p.nwalk, 256, 0, s>>>(p, fold);
+    else k_fold<REWL_F32><<<p.nwalk, 256, 0, s>>>(p, fold);
     return cudaGetLastError();
 }
 
@@ -562,46 +621,6 @@ cudaError_t launch_philox(const uint32_t *d_ctr, uint32_t k0, uint32_t k1, uint3
     uint64_t blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     k_philox<<<(unsigned)blocks, 256, 0, s>>>(d_ctr, k0, k1, d_out, n);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------ table copies ----
-
-__global__ void k_tables_to_double(Params p, double *out)
-{
-    const size_t n = (size_t)p.nwalk * p.T;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t w = i / p.T, b = i % p.T;
-        out[i] = lng_read(p, w * p.tstride + b);
-    }
-}
-
-cudaError_t launch_tables_to_double(const Params &p, double *d_out, cudaStream_t s)
-{
-    k_tables_to_double<<<1024, 256, 0, s>>>(p, d_out);
-    return cudaGetLastError();
-}
-
-__global__ void k_tables_from_double(Params p, const double *in)
-{
-    const size_t n = (size_t)p.nwalk * p.T;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t w = i / p.T, b = i % p.T;
-        const double v = in[i];
-        if (p.precision == REWL_FP64) {
-            p.lng[w * p.tstride + b] = v;
-        } else if (p.precision == REWL_F32) {
-            p.lng1[w * p.tstride + b] = (float)v;
-        } else {
-            const float hi = (float)v;
-            p.lng2[w * p.tstride + b] = make_float2(hi, (float)(v - (double)hi));
-        }
-    }
-}
-
-cudaError_t launch_tables_from_double(const Params &p, const double *d_in, cudaStream_t s)
-{
-    k_tables_from_double<<<1024, 256, 0, s>>>(p, d_in);
     return cudaGetLastError();
 }
 

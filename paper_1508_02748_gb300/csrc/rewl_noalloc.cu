@@ -1,13 +1,13 @@
 // rewl_join_noalloc: the final merge / join / normalisation of librewl for
 // callers that cannot allocate device memory.
 //
-// Who needs it: code that runs where allocation is not allowed or not
-// possible -- inside a region being captured into a CUDA graph, under an
-// external allocator that owns all device memory, or in a process whose
-// memory budget is fixed up front.  Such a caller still owns its inputs and
-// output; what it cannot provide is the join's working memory.  This entry
-// point takes that working memory from one file-scope device array of fixed
-// size, so it calls no allocator at all.
+// Who needs it: callers that may not call cudaMalloc -- a process whose
+// device memory is all owned by an external allocator (a framework's caching
+// pool), or one whose memory budget is fixed up front.  Such a caller still
+// owns its inputs and output; what it cannot provide is the join's working
+// memory.  This entry point takes that working memory from one file-scope
+// device array of fixed size, so it calls no allocator at all.  It reads its
+// error word back and synchronises on the caller's stream before returning.
 //
 // The array: kScratchBytes (8 MiB) of __device__ memory, present
 // on every GPU that loads the library until the process exits.  Its device
@@ -37,7 +37,7 @@ __device__ __align__(256) unsigned char g_join_scratch[kScratchBytes];
 
 std::mutex g_mu;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
-char g_msg[512];
+thread_local char g_msg[512];    // message of this thread's last call
 
 int say(int code, const char *fmt, ...)
 {
@@ -56,6 +56,7 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 using namespace rewl;
 
+// The calling thread's last message (each host thread has its own).
 extern "C" const char *rewl_noalloc_last_error(void) { return g_msg; }
 
 extern "C" int rewl_join_noalloc(const rewl_config *cfg, const double *d_lng, const int32_t *d_H, double *d_out,
@@ -162,6 +163,7 @@ extern "C" int rewl_join_noalloc(const rewl_config *cfg, const double *d_lng, co
     j.gbuf = (double *)(base + o_gbuf);
 
     cudaStream_t s = (cudaStream_t)stream;
+    // a zeroed state has ln f = 0: the join reads the caller's ln g as it is
     if ((ce = cudaMemsetAsync(p.st, 0, sizeof(DevState), s)) != cudaSuccess ||
         (ce = cudaMemcpyAsync((void *)p.rect, rect.data(), sizeof(int4) * d.nwin, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (ce = cudaMemcpyAsync((void *)p.active, active.data(), sizeof(int32_t) * d.nwin, cudaMemcpyHostToDevice, s)) != cudaSuccess ||

@@ -9,44 +9,55 @@
 // h = l + 1 - 2^d (bit k of h = outcome assumed for trial t+k).
 //
 // Per step every lane
-//   1. reads its own trial's site from the ring and the five spins around it
-//      from the committed lattice, corrected for the sites its history flips;
-//      this gives the move (de, dm) of its trial under its history;
+//   1. reads its trial's ring entry and the five spins around its site from
+//      the committed lattice, corrected for the sites its history flips: the
+//      ring entry carries, for each earlier trial of the step, which of the
+//      five positions that trial's site is (a one-hot code made when the
+//      ring was filled), so the correction is one mask and a fold;
 //   2. takes the moves of the earlier trials of its history by shuffle from
-//      the lanes that evaluated them (lane 2^k - 1 + (h mod 2^k) for trial k),
-//      and walks them to find its current bin and the bins visited;
-//   3. decides its own trial (Eq. 1) with the exact ln g values the sequential
-//      chain would see there: value(bin) = table(bin) + visits * ln f.
+//      the lanes that evaluated them and adds them up: its position (E, M)
+//      and the positions after each earlier trial;
+//   3. decides its own trial (Eq. 1) from the values the sequential chain
+//      sees there, ln g(b) = base(b) + (H(b) + visits earlier in the step)
+//      ln f.
 // One ballot gives the true path from the root: a lane is on it iff the
 // ballot bits of its ancestors are the outcomes its history assumes.  Lane k
-// of the path knows the bin the walker is in after trial t+k and posts it in
-// a per-walker mailbox in shared memory; after one warp barrier every lane
-// knows the path's bins, the leaf's (E, M) and its flips, and lane k commits
-// trial k: its spin flip, and the ln g / H update of its bin if that bin is
-// left in this step (first occurrence only, with all its visits).
+// of the path posts the position after trial t+k (and, for a register
+// lattice, the site it flipped) in a per-walker mailbox in shared memory;
+// after one warp barrier every lane knows the path, and the shallowest path
+// lane that ends in each bin the walker leaves writes that bin's new visit
+// count H.  The leaf also posts the count and screen value of the final bin,
+// so the group adopts its new state without another table read.
 //
-// Tables staged in shared memory (double or compensated pairs) are not
-// updated during a launch: H counts the launch's visits Q(b), a bin's value
-// is table(b) + Q(b) ln f, and the counts are folded into the tables when
-// the launch writes them back.  The float screen reads a 32-bit copy of each
-// staged value.
+// Tables (exact formats only; REWL_F32 runs on the thread sampler): ln g(b)
+// = base(b) + max(H(b), 0) ln f, the base fixed during an iteration, so a
+// visit changes H alone and no floating-point table update runs here.  The
+// decision is screened in float from a 32-bit screen per bin, S(b) =
+// base(b) - c_w rounded to nearest (c_w one constant per walker, which
+// cancels in the difference and keeps the screened magnitudes small), and
+// re-taken exactly in double on near-ties.  Tables live in global memory
+// (L1-cached) or, when small, are staged in shared memory for the launch
+// (S and H; the bases are read only by the exact re-decision).
 //
 // The outcome is the sequential chain itself, trial for trial:
 //   - random numbers are drawn per trial index from the TRIAL stream of
 //     Philox4x32-10, independent of the state (a ring of 128 trials per
 //     walker, refilled 64 at a time from the even trial at or below the
 //     launch's first trial);
-//   - table(bin) + visits * ln f is evaluated exactly: fma in double for
-//     REWL_FP64, a compensated (hi, lo) float sum for REWL_F32X2; both equal
-//     the sequential additions whenever ln f = 2^-k and the values stay
-//     within the exact range of the format;
-//   - decisions are screened in float with a margin that bounds the float
-//     rounding (|x - float(x)| < 2^-23 |x| for both table formats) and
-//     re-taken exactly on near-ties (out of line: the exact difference
-//     against the float ln u, and ln u in double only when those two are
-//     within 2^-20 (|ln u| + 1)).
-// The walker's current bin stays in registers (its table value at entry,
-// the visits since then) and is written back when the walker leaves it.
+//   - base(b) + n ln f is evaluated exactly in double (fma; the compensated
+//     pair converts exactly) and equals the sequential additions whenever
+//     ln f = 2^-k and the values stay within 53 (pair: 48) bits;
+//   - the float screen is decided only outside a margin that bounds its
+//     error.  With S within 2^-24 |S| of base - c_w, the count converted to
+//     float within 2^-24 of itself, one rounding in each fma and in the
+//     difference, and the float ln u within 2^-22 (|ln u| + 1) of ln u (u
+//     rounds with relative error below 2^-23, logf errs by at most one ulp),
+//     the screened difference errs by less than
+//         2^-21 (|c| + |n| + |S_c| + |S_n| + |ln u| + 1),
+//     half of the margin M = 2^-20 (|c| + |n| + |S_c| + |S_n| + |ln u|) +
+//     2^-20 used below.  Inside the margin the decision is re-taken from the
+//     exact difference (out of line): against the float ln u where the two
+//     are farther apart than 2^-20 (|ln u| + 1), else against ln u in double.
 #include "rewl_tab.cuh"
 
 namespace rewl {
@@ -59,38 +70,37 @@ constexpr int RING = 128;   // trials buffered per walker
 
 // One buffered trial (16 bytes, one shared-memory vector load).  Everything
 // about a trial that does not depend on the walker's state is computed when
-// the ring is refilled: the site and its four periodic neighbours, and ln u.
+// the ring is refilled.
 struct RingEntry {
-    uint32_t a;    // register lattice: the 6-bit indices of the site and of its up,
-                   //   down, left and right neighbours at bits 0, 6, 12, 18, 24;
-                   // shared lattice: row | col << 8 | up-row << 16 | down-row << 24
-    uint32_t b;    // shared lattice: left-col | right-col << 8
+    uint32_t a;    // five 6-bit fields at bits 0, 6, 12, 18, 24:
+                   //   register lattice: bit indices i*L+j of the site and of its up,
+                   //   down, left and right neighbours;
+                   //   shared lattice: row i, column j, up row, down row, left column
+    uint32_t b;    // bits 0-5: shared lattice: right column; bits 6-25: for lag
+                   //   1..4 (5 bits each), which of (site, up, down, left, right)
+                   //   is the site of trial t - lag (one-hot, or 0)
     uint32_t xu;   // acceptance word
     float lnu;     // ln u in float
 };
 
-// Per-walker exchange area of one step (shared memory): the lanes of a
-// group trade their trial results through it instead of warp shuffles.
+// Per-walker exchange area of one step (shared memory).
 struct Mailbox {
-    int dummy[32];                 // discarded stores of the branch-free write-back
-    int after[8];                  // bin after trial t+k on the true path
-    int leafpos;                   // the leaf's new (e, m)
-    int pad;
-    unsigned long long flips;      // register lattice: the path's flip mask
+    int after[8];                  // position e << 16 | m after trial t+k on the true path
+    int fsite[8];                  // register lattice: bit index flipped by trial t+k, 64 if none
+    int leafq;                     // H of the final bin as read this step (>= 0)
+    float leafs;                   // its screen value
+    int pad[2];
 };
 
 // Eq. 1 decided from the exact values (near-ties of the float screen only);
-// kept out of line so none of it runs in the common case.  The difference
-// delta is exact in double.  The float ln u of the ring (logf of u rounded to
-// float) is within 2^-22 (|ln u| + 1) of ln u: u rounds with relative error
-// below 2^-23 and logf errs by at most 1 ulp (its documented bound).  So
-// outside a band 4x wider the float ln u decides, and only inside it is ln u
-// taken in double (the double logarithm is slow here).
+// kept out of line so none of it runs in the common case.  ccnt and ncnt
+// are the visit counts the chain has at that point; the difference is exact
+// in double.
 template <class TB>
-__device__ __noinline__ int exact_accept(typename TB::Val cbase, int ccnt, typename TB::Val nbase, int ncnt,
+__device__ __noinline__ int exact_accept(const typename TB::Elem *gb, unsigned ci, int ccnt, unsigned ni, int ncnt,
                                          double lnf, uint32_t xu, float lnu32)
 {
-    const double delta = fma((double)ccnt, lnf, TB::exact(cbase)) - fma((double)ncnt, lnf, TB::exact(nbase));
+    const double delta = fma((double)ccnt, lnf, TB::exact(gb[ci])) - fma((double)ncnt, lnf, TB::exact(gb[ni]));
     if (delta >= 0.0) return 1;
     const double lu = (double)lnu32;
     const double band = (fabs(lu) + 1.0) * 0x1p-20;
@@ -99,47 +109,40 @@ __device__ __noinline__ int exact_accept(typename TB::Val cbase, int ccnt, typen
     return log(unit_open_d(xu)) < delta ? 1 : 0;
 }
 
-// The same with staged tables that keep their launch-start values: the base
-// values are read from the staged table here, off the common path.
-template <class TB>
-__device__ __noinline__ int exact_accept_staged(const typename TB::Elem *tl, int cb, int ccnt, int nb, int ncnt,
-                                                double lnf, uint32_t xu, float lnu32)
-{
-    return exact_accept<TB>(TB::load(tl, cb), ccnt, TB::load(tl, nb), ncnt, lnf, xu, lnu32);
-}
-
 template <int G>
 struct TreeShape {
     static constexpr int DEPTH = G == 32 ? 4 : G == 16 ? 3 : G == 8 ? 2 : 1;
 };
 
+// Position code of a site for the relation codes: the bit index (register
+// lattice) or row | column << 6 (shared lattice).
+template <bool REG>
+__device__ __forceinline__ uint32_t site_code(uint32_t a)
+{
+    return REG ? (a & 63u) : (a & 0xFFFu);
+}
+
 }  // namespace
 
 // REG: the lattice (N <= 64 sites, bit i*L + j) is held in a 64-bit register
 // by every lane; otherwise it lives in shared memory, one 32-bit word per row
-// (two for L > 32).
+// (two for L > 32).  SMT: S and H staged in shared memory for the launch.
 template <int WPR, bool SMT, int G, int PREC, bool REG>
 __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, int smem_per_walker)
 {
     using TB = Tab<PREC>;
     using Elem = typename TB::Elem;
-    using Val = typename TB::Val;
     constexpr int DEPTH = TreeShape<G>::DEPTH;
-    // LAZY (tables staged in shared memory, exact formats): the staged ln g
-    // values stay those of the launch start and the shared H array counts the
-    // visits of this launch, Q(b); the value of bin b is table(b) + Q(b) ln f,
-    // folded into the tables once, when they are written back.  No
-    // floating-point update runs per trial (the double update is slow here).
-    constexpr bool LAZY = SMT && PREC != REWL_F32;
     constexpr int GPW = 32 / G;   // walkers per warp
     constexpr unsigned GBITS = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
+    constexpr unsigned RMASK = RING - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gl = lane & (G - 1), grp = lane / G;
     const unsigned gmask = GBITS << (grp * G);
     const int slot = wid * GPW + grp;   // walker slot within the block
     const int w = blockIdx.x * ((blockDim.x >> 5) * GPW) + slot;
-    if (w >= p.nwalk) return;
+    if (w >= p.nwalk || ntrials == 0) return;
     if (!p.active[w / p.W] || p.st->done) return;
 
     unsigned char *base = smem_raw + (size_t)slot * smem_per_walker;
@@ -148,23 +151,21 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     uint32_t *lat = reinterpret_cast<uint32_t *>(base + RING * sizeof(RingEntry) + sizeof(Mailbox));
     const int L = p.L, nwords = L * WPR;
     const int T = p.T;
-    Elem *g_tab = (PREC == REWL_FP64) ? reinterpret_cast<Elem *>(p.lng)
-                : (PREC == REWL_F32X2) ? reinterpret_cast<Elem *>(p.lng2) : reinterpret_cast<Elem *>(p.lng1);
-    g_tab += (size_t)w * p.tstride;
+    const Elem *g_base = reinterpret_cast<const Elem *>(PREC == REWL_FP64 ? (const void *)p.lng : (const void *)p.lng2)
+                       + (size_t)w * p.tstride;
     int32_t *gH = p.H + (size_t)w * p.tstride;
-    Elem *tl;
-    int32_t *tH;
-    if (SMT) {
-        tl = reinterpret_cast<Elem *>(base + RING * sizeof(RingEntry) + sizeof(Mailbox) + ((nwords * 4 + 15) & ~15));
-        tH = reinterpret_cast<int32_t *>(tl + T);
-        for (int k = gl; k < T; k += G) { tl[k] = g_tab[k]; tH[k] = LAZY ? 0 : gH[k]; }
-        if constexpr (LAZY && PREC == REWL_FP64) {
-            float *t32 = reinterpret_cast<float *>(tH + T);
-            for (int k = gl; k < T; k += G) t32[k] = TB::approx(g_tab[k]);
-        }
+    const float *gS = p.scr + (size_t)w * p.tstride;
+    const float *S;
+    int32_t *Hh;
+    if constexpr (SMT) {
+        float *sS = reinterpret_cast<float *>(base + RING * sizeof(RingEntry) + sizeof(Mailbox) + ((nwords * 4 + 15) & ~15));
+        int32_t *sH = reinterpret_cast<int32_t *>(sS + ((T + 3) & ~3));
+        for (int k = gl; k < T; k += G) { sS[k] = gS[k]; sH[k] = gH[k]; }
+        S = sS;
+        Hh = sH;
     } else {
-        tl = g_tab;
-        tH = gH;
+        S = gS;
+        Hh = gH;
     }
     unsigned long long lat64 = 0;
     if (REG) {
@@ -178,8 +179,9 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     const int4 R = p.rect[w / p.W];
     const int wM = p.wM;
     const unsigned spanE = (unsigned)(R.y - R.x), spanM = (unsigned)(R.w - R.z);
+    const unsigned Tm1 = (unsigned)(T - 1);
     const double lnf = p.st->lnf;
-    const float lnf32 = trunc_f(lnf);
+    const float lnf32 = __double2float_rn(lnf);
     const uint32_t N = (uint32_t)p.N;
     const uint32_t divL = p.divL;
 
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
     const int hist = gl + 1 - (1 << dl);
     int srck[DEPTH];
     #pragma unroll
-    for (int k = 0; k < DEPTH; ++k) srck[k] = (1 << k) - 1 + (hist & ((1 << k) - 1));
+    for (int k = 0; k < DEPTH; ++k) srck[k] = grp * G + (1 << k) - 1 + (hist & ((1 << k) - 1));
     // the lane is on the true path iff the ballot bits of its ancestors
     // (lane 2^k - 1 + (h mod 2^k) at depth k < d) are the outcomes its
     // history assumes: anc marks the ancestors, want holds those outcomes
@@ -200,23 +202,21 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             anc |= 1u << a;
             want |= (unsigned)((hist >> k) & 1) << a;
         }
+    // relation fields of the lags whose trials the history accepts: trial
+    // t+k (k < d) is lag d - k of this lane's trial
+    uint32_t sel = 0;
+    #pragma unroll
+    for (int k = 0; k <= DEPTH; ++k)
+        if (k < dl && ((hist >> k) & 1)) sel |= 0x1Fu << (5 * (dl - k - 1));
 
-    // committed state (uniform over the group)
-    int e = p.we[w], m = p.wm[w];
-    int ci = (e - R.x) * wM + (m - R.z);
-    // LAZY: the float screen reads one 32-bit word per bin: the float copy of
-    // a double table (staged after H), the hi word of a compensated pair
-    const float *scr32 = !LAZY ? nullptr
-                       : (PREC == REWL_FP64) ? reinterpret_cast<const float *>(tH + T)
-                                             : reinterpret_cast<const float *>(tl);
-    constexpr int SCR_STRIDE = PREC == REWL_FP64 ? 1 : 2;
-    Val lbase = TB::load(tl, ci);   // table value of the current bin when entered
-    int lq = 0;                     // ln f steps since lbase (LAZY: visits of this launch)
-    int hq = 0;                     // visits of the current bin not yet in H (LAZY: in Q)
-    int hbase = tH[ci];
-    float base32 = TB::approx(lbase);
+    // committed state (uniform over the group); positions are e << 16 | m
+    int P0 = (p.we[w] << 16) | p.wm[w];
+    int ci = ((P0 >> 16) - R.x) * wM + ((P0 & 0xFFFF) - R.z);
+    int lq = max(Hh[ci], 0);        // H of the current bin, visits of this step excluded
+    int hq = 0;                     // visits of the current bin not yet written to H
+    float base32 = S[ci];
     const unsigned long long t0 = p.wt[w];
-    const unsigned r0 = (unsigned)t0 & (RING - 1);
+    const unsigned r0 = (unsigned)t0 & RMASK;
     unsigned u = 0;                 // trials done in this launch
     unsigned ufill = 0;             // ring holds trials [t0 - (t0 & 1), t0 + ufill)
     const unsigned long long c0 = t0 >> 1;   // first Philox call
@@ -243,251 +243,203 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
                         en.a = site | ((iu * L + j) << 6) | ((id * L + j) << 12) | ((i * L + jl) << 18) | ((i * L + jr) << 24);
                         en.b = 0;
                     } else {
-                        en.a = i | (j << 8) | (iu << 16) | (id << 24);
-                        en.b = jl | (jr << 8);
+                        en.a = i | (j << 6) | (iu << 12) | (id << 18) | (jl << 24);
+                        en.b = jr;
                     }
                     en.xu = xu;
                     en.lnu = logf(__fmaf_rn(__uint2float_rn(xu), 0x1p-32f, 0x1p-33f));
-                    ring[(unsigned)(2 * c + hh) & (RING - 1)] = en;
+                    ring[(unsigned)(2 * c + hh) & RMASK] = en;
                 }
+            }
+            __syncwarp(gmask);
+            // relation codes of the 64 new trials to the DEPTH trials before each
+            #pragma unroll
+            for (int r = 0; r < 64 / G; ++r) {
+                const unsigned q = (unsigned)(2 * (c0 + cfill)) + (unsigned)(gl + r * G);
+                const uint32_t a = ring[q & RMASK].a, b = ring[q & RMASK].b;
+                uint32_t pos[5];
+                if (REG) {
+                    #pragma unroll
+                    for (int f = 0; f < 5; ++f) pos[f] = (a >> (6 * f)) & 63u;
+                } else {
+                    const uint32_t row = a & 63u, colbits = a & (63u << 6);
+                    pos[0] = a & 0xFFFu;
+                    pos[1] = ((a >> 12) & 63u) | colbits;
+                    pos[2] = ((a >> 18) & 63u) | colbits;
+                    pos[3] = row | (((a >> 24) & 63u) << 6);
+                    pos[4] = row | ((b & 63u) << 6);
+                }
+                uint32_t rel = 0;
+                #pragma unroll
+                for (int lag = 1; lag <= DEPTH; ++lag) {
+                    const uint32_t f = site_code<REG>(ring[(q - lag) & RMASK].a);
+                    uint32_t oh = 0;
+                    #pragma unroll
+                    for (int k = 0; k < 5; ++k) oh |= (uint32_t)(f == pos[k]) << k;
+                    rel |= oh << (5 * (lag - 1));
+                }
+                ring[q & RMASK].b = b | (rel << 6);
             }
             cfill += 32;
             ufill = 2 * cfill - (unsigned)(t0 & 1ull);
             __syncwarp(gmask);
         }
-        if (!LAZY && lq >= (1 << 22)) {   // keep the float screen's counts exact (LAZY
-                                          // launches run fewer than 2^22 trials)
-            lbase = TB::add(lbase, lq, lnf, lnf32);
-            lq = 0;
-            base32 = TB::approx(lbase);
-        }
         const unsigned left = ntrials - u;
         const int D = left > (unsigned)DEPTH ? DEPTH : (int)left - 1;
         const unsigned rb = r0 + u;
 
-        // ---- 1. own trial under own history
-        const RingEntry me = ring[(rb + dl) & (RING - 1)];
-        uint32_t sa[DEPTH + 1];      // site words of trials t .. t+DEPTH (uniform)
-        #pragma unroll
-        for (int k = 0; k <= DEPTH; ++k) sa[k] = ring[(rb + k) & (RING - 1)].a;
-        uint32_t sbit, bu, bd, bl, br;
-        unsigned long long fm = 0;   // register lattice: sites flipped by the history
+        // ---- 1. own trial under own history: the five spins
+        const RingEntry me = ring[(rb + dl) & RMASK];
+        uint32_t v5;
         if (REG) {
-            #pragma unroll
-            for (int k = 0; k < DEPTH; ++k)
-                if (k < dl && ((hist >> k) & 1)) fm ^= 1ull << (sa[k] & 63u);   // a site may flip twice
-            const unsigned long long v = lat64 ^ fm;
-            sbit = (uint32_t)(v >> (me.a & 63u)) & 1u;
-            bu = (uint32_t)(v >> ((me.a >> 6) & 63u)) & 1u;
-            bd = (uint32_t)(v >> ((me.a >> 12) & 63u)) & 1u;
-            bl = (uint32_t)(v >> ((me.a >> 18) & 63u)) & 1u;
-            br = (uint32_t)(v >> ((me.a >> 24) & 63u)) & 1u;
+            v5 = ((uint32_t)(lat64 >> (me.a & 63u)) & 1u)
+               | (((uint32_t)(lat64 >> ((me.a >> 6) & 63u)) & 1u) << 1)
+               | (((uint32_t)(lat64 >> ((me.a >> 12) & 63u)) & 1u) << 2)
+               | (((uint32_t)(lat64 >> ((me.a >> 18) & 63u)) & 1u) << 3)
+               | (((uint32_t)(lat64 >> ((me.a >> 24) & 63u)) & 1u) << 4);
         } else {
-            const int i = me.a & 255, j = (me.a >> 8) & 255, iu = (me.a >> 16) & 255, id = me.a >> 24;
-            const int jl = me.b & 255, jr = (me.b >> 8) & 255;
-            const int qj = (WPR == 1) ? 0 : (j >> 5);
+            const uint32_t i = me.a & 63u, j = (me.a >> 6) & 63u, iu = (me.a >> 12) & 63u, id = (me.a >> 18) & 63u;
+            const uint32_t jl = (me.a >> 24) & 63u, jr = me.b & 63u;
+            const uint32_t qj = (WPR == 1) ? 0 : (j >> 5);
             const uint32_t wc = lat[i * WPR + qj], wu = lat[iu * WPR + qj], wd = lat[id * WPR + qj];
-            sbit = (wc >> (j & 31)) & 1u;
-            bu = (wu >> (j & 31)) & 1u;
-            bd = (wd >> (j & 31)) & 1u;
-            bl = ((WPR == 1 ? wc : lat[i * WPR + (jl >> 5)]) >> (jl & 31)) & 1u;
-            br = ((WPR == 1 ? wc : lat[i * WPR + (jr >> 5)]) >> (jr & 31)) & 1u;
-            const uint32_t p_s = i | (j << 8), p_u = iu | (j << 8), p_d = id | (j << 8);
-            const uint32_t p_l = i | (jl << 8), p_r = i | (jr << 8);
-            #pragma unroll
-            for (int k = 0; k < DEPTH; ++k) {
-                if (k < dl && ((hist >> k) & 1)) {
-                    const uint32_t f = sa[k] & 0xFFFFu;
-                    sbit ^= (f == p_s);
-                    bu ^= (f == p_u);
-                    bd ^= (f == p_d);
-                    bl ^= (f == p_l);
-                    br ^= (f == p_r);
-                }
-            }
+            const uint32_t wl = (WPR == 1) ? wc : lat[i * WPR + (jl >> 5)];
+            const uint32_t wr = (WPR == 1) ? wc : lat[i * WPR + (jr >> 5)];
+            v5 = ((wc >> (j & 31)) & 1u) | (((wu >> (j & 31)) & 1u) << 1) | (((wd >> (j & 31)) & 1u) << 2)
+               | (((wl >> (jl & 31)) & 1u) << 3) | (((wr >> (jr & 31)) & 1u) << 4);
         }
-        const int nup = (int)(bu + bd + bl + br);
-        const int de_own = sbit ? nup - 2 : 2 - nup;
-        const int dm_own = sbit ? -1 : 1;
-        const int pack = (de_own + 2) | ((dm_own + 1) << 3);
+        {
+            const uint32_t corr = (me.b >> 6) & sel;
+            v5 ^= (corr ^ (corr >> 5) ^ (corr >> 10) ^ (corr >> 15)) & 0x1Fu;
+        }
+        const int sup = (int)(v5 & 1u);
+        const int nup = __popc(v5 & 0x1Eu);
+        const int de_own = sup ? nup - 2 : 2 - nup;
+        const int dm_own = sup ? -1 : 1;
+        const int pk = de_own * 65536 + dm_own;   // move as a position difference
 
         // ---- 2. the history's earlier trials: the move of trial k under the
-        // history's first k outcomes is the own move of lane 2^k - 1 + (h mod 2^k),
-        // taken by shuffle; a history that accepts a move out of the window is
-        // never the true path, and its bins are clamped below only to keep its
-        // reads in bounds
-        int ce = e, cm = m, cbin = ci;
-        int vb[DEPTH];               // bin after each earlier trial (-1 past the own depth)
+        // history's first k outcomes is the own move of lane 2^k - 1 + (h mod 2^k);
+        // a history that accepts a move out of the window is never the true path
+        int Pc = P0;
+        int vb[DEPTH];               // position after each earlier trial (-1 past the own depth)
         #pragma unroll
         for (int k = 0; k < DEPTH; ++k) {
-            const int pk = __shfl_sync(gmask, pack, grp * G + srck[k]);
-            if (k < dl && ((hist >> k) & 1)) {
-                const int de = (pk & 7) - 2, dm = ((pk >> 3) & 3) - 1;
-                ce += de;
-                cm += dm;
-                cbin += de * wM + dm;
-            }
-            vb[k] = k < dl ? cbin : -1;
+            const int x = __shfl_sync(gmask, pk, srck[k]);
+            if ((hist >> k) & 1) Pc += x;
+            vb[k] = k < dl ? Pc : -1;
         }
+        const int Pn = Pc + pk;
+        const int ce = Pc >> 16, cm = Pc & 0xFFFF;
+        const int cidx = (ce - R.x) * wM + (cm - R.z);
+        const int nidx = cidx + de_own * wM + dm_own;
+        const bool live = dl <= D && (unsigned)(ce + de_own - R.x) <= spanE && (unsigned)(cm + dm_own - R.z) <= spanM;
 
-        // ---- 3. decision of the own trial (Eq. 1)
-        const int en_o = ce + de_own, mn_o = cm + dm_own;
-        const int nbin = cbin + de_own * wM + dm_own;
-        const bool live = dl <= D && (unsigned)(en_o - R.x) <= spanE && (unsigned)(mn_o - R.z) <= spanM;
-        const int cb = min(max(cbin, 0), T - 1), nb = min(max(nbin, 0), T - 1);
+        // ---- 3. decision of the own trial (Eq. 1); off-path lanes may hold
+        // positions outside the window, so their reads are clamped
+        const unsigned cu = min((unsigned)cidx, Tm1), nu = min((unsigned)nidx, Tm1);
+        const float cs_m = S[cu], ns_m = S[nu];
+        const int hc = max(Hh[cu], 0), hn = max(Hh[nu], 0);
         int vcur = 0, vnew = 0;
         #pragma unroll
         for (int k = 0; k < DEPTH; ++k) {
-            vcur += (vb[k] == cb);
-            vnew += (vb[k] == nb);
+            vcur += (vb[k] == Pc);
+            vnew += (vb[k] == Pn);
         }
-        const bool c0b = cb == ci, n0b = nb == ci;
-        Val cbase, nbase;
-        float cb32, nb32;
-        if constexpr (LAZY) {
-            cb32 = c0b ? base32 : scr32[cb * SCR_STRIDE];
-            nb32 = n0b ? base32 : scr32[nb * SCR_STRIDE];
-        } else {
-            const Val tc = TB::load(tl, cb), tn = TB::load(tl, nb);
-            cbase = c0b ? lbase : tc;
-            nbase = n0b ? lbase : tn;
-            cb32 = c0b ? base32 : TB::approx(tc);
-            nb32 = n0b ? base32 : TB::approx(tn);
-        }
-        const int qc = LAZY ? tH[cb] : 0, qn = LAZY ? tH[nb] : 0;
-        const int ccnt = vcur + (c0b ? lq : qc), ncnt = vnew + (n0b ? lq : qn);
-        const float c32 = __fmaf_rn((float)ccnt, lnf32, cb32);
-        const float n32 = __fmaf_rn((float)ncnt, lnf32, nb32);
-        const float d32 = c32 - n32;
-        const float M = (fabsf(c32) + fabsf(n32) + fabsf(cb32) + fabsf(nb32) + fabsf(me.lnu)) * 0x1p-20f + 0x1p-20f;
+        const bool c0b = Pc == P0, n0b = Pn == P0;
+        const float cs = c0b ? base32 : cs_m, ns = n0b ? base32 : ns_m;
+        const int ccnt = vcur + (c0b ? lq : hc), ncnt = vnew + (n0b ? lq : hn);
+        const float c32 = __fmaf_rn(__int2float_rn(ccnt), lnf32, cs);
+        const float n32 = __fmaf_rn(__int2float_rn(ncnt), lnf32, ns);
+        const float d32 = __fsub_rn(c32, n32);
+        const float M = __fmaf_rn(fabsf(c32) + fabsf(n32) + fabsf(cs) + fabsf(ns) + fabsf(me.lnu), 0x1p-20f, 0x1p-20f);
         int acc = (me.lnu < d32 - M) ? 1 : 0;
-        if constexpr (PREC == REWL_F32) {
-            // plain float: the values the walker sees are the rounded sums
-            acc = (me.lnu < TB::add(cbase, ccnt, lnf, lnf32) - TB::add(nbase, ncnt, lnf, lnf32)) ? 1 : 0;
-        } else if (live && !acc && !(me.lnu > d32 + M)) {
-            // LAZY: the current bin's base is its staged value too (lbase == tl[ci])
-            if constexpr (LAZY) acc = exact_accept_staged<TB>(tl, cb, ccnt, nb, ncnt, lnf, me.xu, me.lnu);
-            else acc = exact_accept<TB>(cbase, ccnt, nbase, ncnt, lnf, me.xu, me.lnu);
-        }
+        if (live && !acc && !(me.lnu > d32 + M))
+            acc = exact_accept<TB>(g_base, cu, ccnt, nu, ncnt, lnf, me.xu, me.lnu);
         acc = live ? acc : 0;
-        const int after = acc ? nbin : cbin;   // bin after the own trial, under the own history
+        const int after = acc ? Pn : Pc;          // position after the own trial, under the own history
 
         // ---- the true path: the lanes whose ancestors decided as their history assumes
         const unsigned bal = (__ballot_sync(gmask, acc) >> (grp * G)) & GBITS;
         const bool onp = dl <= D && ((bal ^ want) & anc) == 0u;
-        const bool is_leaf = onp && dl == D;
 
         // ---- commit: the on-path lane of depth k takes trial t+k
-        if (onp) box->after[dl] = after;
-        if (is_leaf) {
-            box->leafpos = ((acc ? en_o : ce) << 13) | (acc ? mn_o : cm);
-            if (REG) box->flips = fm ^ (acc ? (1ull << (me.a & 63u)) : 0ull);
+        const int aq = acc ? hn : hc;             // H of `after` as read (unless it is the current bin)
+        if (onp) {
+            box->after[dl] = after;
+            if (REG) box->fsite[dl] = acc ? (int)(me.a & 63u) : 64;
+            if (dl == D) {
+                box->leafq = aq;
+                box->leafs = acc ? ns : cs;
+            }
         }
         __syncwarp(gmask);
         int av[DEPTH + 1];
         #pragma unroll
         for (int k = 0; k <= DEPTH; ++k) av[k] = k <= D ? box->after[k] : -1;
-        const int lp = box->leafpos;
-        const int ne = lp >> 13, nm = lp & 0x1FFF;
-        const int C = (ne - R.x) * wM + (nm - R.z);
+        const int C = box->after[D];
         int cC = 0;
         bool b0_seen = false;
         #pragma unroll
         for (int k = 0; k <= DEPTH; ++k) {
             cC += (av[k] == C);
-            b0_seen |= (av[k] == ci);
+            b0_seen |= (av[k] == P0);
         }
         if (REG) {
-            lat64 ^= box->flips;
+            #pragma unroll
+            for (int k = 0; k <= DEPTH; ++k) {
+                if (k <= D) {
+                    const int f = box->fsite[k];
+                    lat64 ^= (unsigned long long)(f < 64) << (f & 63);
+                }
+            }
         } else if (onp && acc) {
-            const int fi = me.a & 255, fj = (me.a >> 8) & 255;
+            const uint32_t fi = me.a & 63u, fj = (me.a >> 6) & 63u;
             atomicXor(&lat[fi * WPR + ((WPR == 1) ? 0 : (fj >> 5))], 1u << (fj & 31));
         }
-        // first visit of this lane's bin among the path's trials, and its count
-        bool firstv = true;
-        int cntv = 0;
-        #pragma unroll
-        for (int k = 0; k <= DEPTH; ++k) {
-            if (k < dl && av[k] == after) firstv = false;
-            cntv += (av[k] == after);
-        }
-        // write-back of a bin the walker leaves in this step (all its visits),
-        // by the shallowest on-path lane that ended in it
+        // write-back of the bins the walker leaves in this step: the shallowest
+        // on-path lane that ended in such a bin writes its H with all its visits
+        // of the step; lane G-1 (never on the path) writes the start bin when
+        // it is left without being visited again
         {
+            bool firstv = true;
+            int cntv = 0;
+            #pragma unroll
+            for (int k = 0; k <= DEPTH; ++k) {
+                if (k < dl && av[k] == after) firstv = false;
+                cntv += (av[k] == after);
+            }
             const bool own = onp && firstv && after != C;
-            const bool entry_left = gl == G - 1 && C != ci && !b0_seen && hq > 0;
-            if (LAZY) {
-                // branch-free: lanes with nothing to write store to their own
-                // slot of the mailbox (the bin index is clamped because a lane
-                // off the true path may hold a bin outside the window)
-                const int Xw = min(max(own ? after : ci, 0), T - 1);
-                const int nq = (own ? cntv : 0) + (Xw == ci ? lq : tH[Xw]);
-                int *dst = (own || entry_left) ? &tH[Xw] : &box->dummy[gl];
-                *dst = nq;
-            } else if (own || entry_left) {
-                const int Xw = own ? after : ci;
-                const bool isci = Xw == ci;
-                const int cnt = own ? cntv : 0;
-                const Val v0 = isci ? lbase : TB::load(tl, Xw);
-                const int h0 = isci ? hbase : tH[Xw];
-                const int nv = cnt + (isci ? lq : 0), nh = cnt + (isci ? hq : 0);
-                const long long hv = (long long)(h0 < 0 ? 0 : h0) + nh;
-                if (hv > 0x7FFFFFFFll) err = 1;
-                tl[Xw] = TB::add(v0, nv, lnf, lnf32);
-                tH[Xw] = (int32_t)hv;
+            const bool entry_left = gl == G - 1 && C != P0 && !b0_seen && hq > 0;
+            const unsigned aidx = acc ? nu : cu;
+            const int val = own ? cntv + (after == P0 ? lq : aq) : lq;
+            if (own || entry_left) {
+                Hh[own ? aidx : (unsigned)ci] = val;
+                err |= val < 0;
             }
         }
         // the group adopts the state after the last trial
-        e = ne;
-        m = nm;
         {
-            const bool same = C == ci;
-            const int hC = tH[C];
-            float bC;
-            if constexpr (LAZY) {
-                bC = scr32[C * SCR_STRIDE];
-            } else {
-                const Val lC = TB::load(tl, C);
-                bC = TB::approx(lC);
-                lbase = same ? lbase : lC;
-            }
-            hbase = same ? hbase : hC;
-            base32 = same ? base32 : bC;
-            lq = same ? lq + cC : cC + (LAZY ? hC : 0);
+            const bool same = C == P0;
+            const int nlq = same ? lq + cC : box->leafq + cC;
+            const float ns32 = box->leafs;
             hq = same ? hq + cC : cC;
-            ci = C;
+            lq = nlq;
+            err |= nlq < 0;
+            if (!same) {
+                base32 = ns32;
+                ci = ((C >> 16) - R.x) * wM + ((C & 0xFFFF) - R.z);
+            }
+            P0 = C;
         }
         __syncwarp(gmask);
         u += (unsigned)(D + 1);
     }
 
     // ---- flush the current bin and the state
-    if (gl == 0 && hq > 0) {
-        if (LAZY) {
-            tH[ci] = lq;
-        } else {
-            const long long hv = (long long)(hbase < 0 ? 0 : hbase) + hq;
-            if (hv > 0x7FFFFFFFll) err = 1;
-            tl[ci] = TB::add(lbase, lq, lnf, lnf32);
-            tH[ci] = (int32_t)hv;
-        }
-    }
+    if (gl == 0 && hq > 0) Hh[ci] = lq;
     __syncwarp(gmask);
-    if (LAZY) {
-        // fold the visits of this launch into the tables: bins not visited
-        // keep their values and H (never visited: -1)
-        for (int k = gl; k < T; k += G) {
-            const int q = tH[k];
-            if (q > 0) {
-                const int h0 = gH[k];
-                const long long hv = (long long)(h0 < 0 ? 0 : h0) + q;
-                if (hv > 0x7FFFFFFFll) err = 1;
-                g_tab[k] = TB::add(tl[k], q, lnf, lnf32);
-                gH[k] = (int32_t)hv;
-            }
-        }
-    } else if (SMT) {
-        for (int k = gl; k < T; k += G) { g_tab[k] = tl[k]; gH[k] = tH[k]; }
+    if constexpr (SMT) {
+        for (int k = gl; k < T; k += G) gH[k] = Hh[k];
     }
     if (REG) {
         for (int r = gl; r < L; r += G)
@@ -496,28 +448,29 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         for (int k = gl; k < nwords; k += G) p.spins[(size_t)k * p.nwalk + w] = lat[k];
     }
     if (gl == 0) {
-        p.we[w] = e;
-        p.wm[w] = m;
+        p.we[w] = P0 >> 16;
+        p.wm[w] = P0 & 0xFFFF;
         p.wt[w] = t0 + u;
     }
     err = __any_sync(gmask, err);
     if (gl == 0 && err) atomicOr(&p.st->error, ERR_OVERFLOW);
 }
 
-// Shared memory per walker: ring, mailbox, lattice (16-byte padded) and, when staged,
-// the tables (8-byte ln g entries in either format, 4-byte H, and for double
-// tables a 4-byte float copy the screen reads).
+// Shared memory per walker: ring, mailbox, lattice (16-byte padded) and, when
+// staged, S (4 bytes per bin, padded to 16 bytes) and H (4 bytes per bin).
 size_t tree_smem_per_warp(const Params &p, bool smt)
 {
     size_t b = RING * sizeof(RingEntry) + sizeof(Mailbox) + (((size_t)p.nwords * 4 + 15) & ~(size_t)15);
-    if (smt) b += (size_t)p.T * (8 + sizeof(int32_t) + (p.precision == REWL_FP64 ? sizeof(float) : 0));
+    if (smt) b += (((size_t)p.T + 3) & ~(size_t)3) * 4 + (size_t)p.T * 4;
     return (b + 15) & ~(size_t)15;
 }
 
 // group: lanes per walker (8, 16 or 32); warps: warps per block.  One
 // launch runs fewer than 2^31 trials per walker (launch_sweep splits).
+// Exact table formats only.
 cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int warps, bool smt, cudaStream_t s)
 {
+    if (p.precision != REWL_FP64 && p.precision != REWL_F32X2) return cudaErrorInvalidValue;
     if (group != 8 && group != 16 && group != 32) group = 32;
     const size_t per = tree_smem_per_warp(p, smt);
     const int gpw = 32 / group;
@@ -549,8 +502,7 @@ cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int 
     return go(k_sweep_tree<W_, S_, 8, P_, false>);
 #define REWL_TREE_P(W_, S_)                                                \
     if (p.precision == REWL_FP64) { REWL_TREE_G(W_, S_, REWL_FP64) }       \
-    else if (p.precision == REWL_F32X2) { REWL_TREE_G(W_, S_, REWL_F32X2) } \
-    else { REWL_TREE_G(W_, S_, REWL_F32) }
+    else { REWL_TREE_G(W_, S_, REWL_F32X2) }
     if (p.wpr == 1) {
         if (smt) { REWL_TREE_P(1, true) } else { REWL_TREE_P(1, false) }
     } else {
