@@ -23,7 +23,13 @@ then a rational function of y = e^{2K}, and Z y^{-N} = sum_e g(e) z^e with
 z = y^{-2} = e^{-4K} and e = (E + 2N)/4.  The coefficients are recovered by
 evaluating at N+1 points z_k = exp(2 pi i (k + 1/2)/(N+1)) (the half step
 keeps y away from the poles y = +-1) and applying the inverse discrete
-Fourier transform, in mpmath at N log10(2) + 40 digits.
+Fourier transform, in mpmath at N log10(2) + 40 digits: coefficient e is
+(1/(N+1)) Re sum_k Z(z_k) w_e^(k + 1/2) with w_e = exp(-2 pi i e/(N+1)),
+summed in Horner form in powers of w_e.  Only e <= N/2 is summed: g(e) =
+g(N - e) for even L (E -> -E maps the torus's ferromagnetic and
+antiferromagnetic states onto each other).  Point evaluations and
+coefficients can be spread over worker processes (``workers``); each is
+the same sum.
 
 Checked in the test suite against brute-force enumeration (L = 4) and the
 transfer matrix (L = 6, 8) from ``exact.c``.
@@ -92,40 +98,60 @@ def _partition_scaled(L: int, y):
     return Z / y ** N
 
 
-def exact_gE(L: int) -> list[int]:
+def _point(args):
+    L, k, P, dps = args
+    with mpmath.workdps(dps):
+        z = mpmath.expjpi(2 * (k + mpmath.mpf(1) / 2) / P)
+        return _partition_scaled(L, 1 / mpmath.sqrt(z))
+
+
+def _coefficient(args):
+    full, e, P, dps = args
+    with mpmath.workdps(dps):
+        w = mpmath.expjpi(-2 * mpmath.mpf(e) / P)
+        acc = mpmath.mpc(0)
+        for k in range(P - 1, -1, -1):
+            acc = acc * w + full[k]
+        acc *= mpmath.expjpi(-mpmath.mpf(e) / P)          # w^(1/2)
+        return int(mpmath.nint(acc.real / P))
+
+
+def exact_gE(L: int, workers: int = 1) -> list[int]:
     """Exact g(e), e = 0..N (E = 4e - 2N), as Python integers; even L >= 4."""
     if L < 4 or L % 2:
         raise ValueError("exact_gE needs even L >= 4")
     N = L * L
     P = N + 1
     dps = int(N * math.log10(2)) + 40
+    # Real coefficients: P(conj z) = conj P(z), so half of the points suffice;
+    # z_{P-1-k} = conj(z_k) because (P-1-k+1/2) = P - (k+1/2).
+    half = P // 2 + 1
+    pts = [(L, k, P, dps) for k in range(half)]
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            vals = pool.map(_point, pts, chunksize=max(1, half // (8 * workers)))
+    else:
+        vals = [_point(a) for a in pts]
     with mpmath.workdps(dps):
-        vals = []
-        # Real coefficients: P(conj z) = conj P(z), so half of the points suffice.
-        half = P // 2 + 1
-        for k in range(half):
-            z = mpmath.expjpi(2 * (k + mpmath.mpf(1) / 2) / P)
-            y = 1 / mpmath.sqrt(z)
-            vals.append(_partition_scaled(L, y))
         full = [None] * P
         for k in range(half):
             full[k] = vals[k]
-            # z_{P-1-k} = conj(z_k) because (P-1-k+1/2) = P - (k+1/2)
             full[P - 1 - k] = mpmath.conj(vals[k])
-        out = []
-        for e in range(P):
-            acc = mpmath.mpc(0)
-            for k in range(P):
-                acc += full[k] * mpmath.expjpi(-2 * (k + mpmath.mpf(1) / 2) * e / P)
-            v = acc.real / P
-            out.append(int(mpmath.nint(v)))
-    return out
+    es = [(full, e, P, dps) for e in range(N // 2 + 1)]
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            lo = pool.map(_coefficient, es, chunksize=max(1, len(es) // (8 * workers)))
+    else:
+        lo = [_coefficient(a) for a in es]
+    return lo + lo[:P - len(lo)][::-1]
 
 
-def exact_lngE(L: int) -> list[float]:
+def exact_lngE(L: int, workers: int = 1) -> list[float]:
     """ln g(e) in double precision (-inf where g(e) = 0)."""
     out = []
-    for g in exact_gE(L):
+    for g in exact_gE(L, workers):
         out.append(-math.inf if g == 0 else _log_int(g))
     return out
 

@@ -28,13 +28,14 @@ def write_gEM_L8():
 
 
 def write_lngE(L):
-    v = exact_lngE(L)
+    v = exact_lngE(L, workers=os.cpu_count() or 1)
     with open(os.path.join(HERE, f"lngE_L{L}.txt"), "w") as f:
         for x in v:
             f.write(("-inf" if x == float("-inf") else repr(float(x))) + "\n")
 
 
 if __name__ == "__main__":
+    # worker processes re-import this module: keep the work under this guard
     targets = sys.argv[1:] or ["8", "16", "32"]
     for t in targets:
         L = int(t)
