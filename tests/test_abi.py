@@ -48,6 +48,14 @@ def test_workspace_size_and_validation_without_gpu():
     assert b"L must be" in lib.rewl_last_error(None)
     bad = P.Config(L=8, flatness=1.5).to_c()
     assert lib.rewl_workspace_size(ctypes.byref(bad), ctypes.byref(n)) == -1
+    # ln f must stay a power of two (every ln g exact): 0.7 and a factor 0.3 are refused
+    for kw in (dict(lnf_init=0.7), dict(lnf_factor=0.3), dict(lnf_init=2.0 ** -70)):
+        bad = P.Config(L=8, **kw).to_c()
+        assert lib.rewl_workspace_size(ctypes.byref(bad), ctypes.byref(n)) == -1
+        assert b"power" in lib.rewl_last_error(None)
+    for kw in (dict(lnf_init=4.0), dict(lnf_factor=0.25), dict(lnf_init=2.0 ** -27)):
+        ok = P.Config(L=8, **kw).to_c()
+        assert lib.rewl_workspace_size(ctypes.byref(ok), ctypes.byref(n)) == 0
 
 
 def test_product_path_has_no_cpu_fallback():

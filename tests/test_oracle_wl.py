@@ -121,7 +121,12 @@ def test_flatness_rule_and_advance():
 
 def test_serial_wl_L4_converges_to_enumeration():
     """Plain serial 2D WL over the whole (E, M) range, ln f 1 -> 1e-6 (the
-    paper's serial WL of Sec. 2 at L = 4) reproduces the exact g(E, M)."""
+    paper's serial WL of Sec. 2 at L = 4) reproduces the exact g(E, M).
+
+    One walker at 80% flatness lands at a mean relative error of the E
+    marginal near 1e-2 (measured over 8 seeds with this check interval: mean
+    1.6e-2, largest 2.5e-2), above the 5e-3 that REWL with several walkers
+    per window reaches; the bounds below are that distribution's."""
     g = oracle.enumerate_gEM(4)
     gE = g.sum(axis=1)
     lgE, lgEM = _lg(gE), _lg(g)
@@ -139,8 +144,26 @@ def test_serial_wl_L4_converges_to_enumeration():
         signed.append((mE[occ] - lgE[occ]).mean())
         big = g > 1
         assert np.abs(J[big] - lgEM[big]).max() < 0.25
-    assert max(mean_eps) < 0.03
+    assert max(mean_eps) < 0.026
+    assert np.mean(mean_eps) < 0.018
     assert abs(np.mean(signed)) < 0.02
+
+
+def test_L4_sixteen_walkers_meet_error_gate():
+    """The same run with 16 walkers in the one window, merged at the end
+    (Sec. 2): the mean relative error of the E marginal against the
+    enumeration falls below 5e-3 (largest over 64 seeds: 4.0e-3)."""
+    g = oracle.enumerate_gEM(4)
+    gE = g.sum(axis=1)
+    lgE = _lg(gE)
+    for rep in range(2):
+        r = OracleREWL(OracleConfig(L=4, walkers_per_window=16, exchange_interval=1000, seed=20151811 + rep))
+        inf = _run_to_done(r)
+        assert inf["done"] and inf["iter"] == 21
+        J, _, _ = r.join()
+        mE = oracle.marginal_e(J)
+        ok = gE > 1
+        assert (np.abs(mE[ok] - lgE[ok]) / lgE[ok]).mean() < 5e-3
 
 
 def test_serial_wl_L5_odd_lattice():
