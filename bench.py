@@ -5,21 +5,32 @@
 One step is one cycle of the whole sampling path on the synthetic workload:
 every walker does `exchange_interval` single-spin-flip trials (Eq. 1 and the
 update of Sec. 2), one replica-exchange sweep (Eq. 2) and the flatness check /
-iteration advance (Sec. 2-3).  The default workload is 2D REWL of the 8 x 8
-periodic Ising model: 3 x 3 (E, M) windows at 75% overlap, 4 walkers per
-window, exchange every 10^4 trials per walker.
+iteration advance (Sec. 2-3).  The default workload is batched 2D REWL of the
+32 x 32 periodic Ising model: 16 x 4 (E, M) windows at 75% overlap, 32 walkers
+per window (2048 walkers), exchange every 10^4 trials per walker, FP64 ln g.
+
+Timed state: the run first advances through its own cycles, untimed, for
+--warm-seconds of wall time (or restores a saved run with --checkpoint), so
+the timed cycles are not the first cycles of iteration 0; the line states the
+iteration and ln f they ran at.
 
 value    trials/s with the run resident in HBM, CUDA events on the run's stream
          around each step, L2 flushed (256 MiB write) between steps;
+plain    the same cycles in the plain one-walker-per-launch form (one
+         single-thread launch per walker over 4 streams, host-driven exchange
+         and check, no graph), trials/s over --plain-cycles cycles;
 e2e      the same metric through the C ABI with host buffers: creation from
          host spin bytes (host->device), K synchronous steps each reading the
          run status back (device->host), and the joined ln g(E,M) copied to
          host memory, wall clock;
-roofline the sampling kernel (the dominant one) against the ALU peak:
-         algorithmic integer/float operations per trial x trials per launch /
-         mean launch time from its own CUDA events in the timed steps;
-cpu_baseline the CPU oracle (test infrastructure, single thread) on a bounded
-         sample of the same workload.
+roofline the sampling kernel (the dominant one) against the integer-logic
+         issue rate measured on this GPU (rewl_measure_peaks): algorithmic
+         integer/float operations per trial x trials per launch / mean launch
+         time from its own CUDA events in the timed steps; the memory side
+         (algorithmic bytes per trial against the measured shared-memory
+         bandwidth) beside it;
+cpu_baseline the CPU oracle (test infrastructure) on every host core: one
+         process per core, each running a bounded sample of the workload.
 With --impl reference the CPU oracle is the timed implementation.
 Under torchrun with N > 1 ranks each rank runs an independent replica of the
 run on its own GPU (the method's windows share one GPU; replicas only).
@@ -49,10 +60,16 @@ METRIC = "WL spin-flip trials/s & time-to-ln f=1e-6 at fixed ln g error, batched
 # the screened acceptance (~10) and the bookkeeping of ln g / H (~8).
 OPS_PER_TRIAL = 120
 
+# Algorithmic bytes per trial to shared memory / L1 (the method's own
+# traffic): lattice 12 B read + 4 B written on an accepted flip, table 24 B
+# (ln g of the proposed bin 8 B, ln g and H of the current bin read and
+# written 16 B).
+BYTES_PER_TRIAL = 40
+
 # DRAM bytes (read + write) per launch of the sampling kernel from one ncu
-# capture (profiles/k_sweep_tree_rewl_L8_3x3_w4.md), keyed by workload, kernel
-# and table format, valid only for the kernel sources they were taken on
-# (hash of the files below); any other case reports null.
+# capture (the profiles directory has the capture's summary), keyed by
+# workload, kernel and table format, valid only for the kernel sources they
+# were taken on (hash of the files below); any other case reports null.
 TRAFFIC_SOURCES = ("paper_1508_02748_gb300/csrc/rewl_sweep_tree.cu", "paper_1508_02748_gb300/csrc/rewl_tab.cuh",
                    "paper_1508_02748_gb300/csrc/rewl_internal.cuh")
 TRAFFIC = {("rewl_L8_3x3_w4", "k_sweep_tree", "fp64", "ae409ff7080ec0e0"): 845568 + 0}
@@ -72,13 +89,19 @@ FALLBACK_SMS = 152
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default=workloads.REWL_L8.name,
+    ap.add_argument("--workload", default=workloads.REWL_L32.name,
                     choices=sorted(workloads.ALL) + [workloads.BATCH_NAME])
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the peak microbenchmarks (derived ALU peak)")
+    ap.add_argument("--warm-seconds", type=float, default=20.0,
+                    help="untimed cycles of the run itself before the timed ones (wall seconds)")
+    ap.add_argument("--checkpoint", default=None, help="time a run restored from this checkpoint (rewl_save)")
+    ap.add_argument("--plain-cycles", type=int, default=1,
+                    help="cycles of the plain one-walker-per-launch form timed after the batched ones (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tiling")
     ap.add_argument("--lanes", type=int, default=None, choices=[8, 16, 32],
@@ -197,59 +220,113 @@ class ClockSampler:
 
 # -------------------------------------------------------------- CPU oracle --
 
-def oracle_rate(w, seconds: float) -> dict:
-    """Trials/s of the CPU oracle on a bounded sample: the workload's run,
-    whole cycles until `seconds` of CPU time have passed."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_walkers(w, table_budget_bytes: int = 256 << 20) -> int:
+    """Walkers per window of the CPU sample: the workload's geometry with at
+    most `table_budget_bytes` of oracle tables per process (12 bytes per bin
+    and walker), at least one walker per window."""
+    import math as _m
+    B = w.N + 1
+
+    def width(n, o):
+        return B if n == 1 else min(B, _m.ceil(B / (1 + (n - 1) * (1 - o))))
+    per_walker = width(w.n_win_E, w.overlap_E) * width(w.n_win_M, w.overlap_M) * 12
+    nwin = w.n_win_E * w.n_win_M
+    return max(1, min(w.walkers_per_window, table_budget_bytes // (per_walker * nwin)))
+
+
+def _oracle_cfg(w, wpw: int, seed: int):
     import oracle
-    ocfg = oracle.OracleConfig(L=w.L, n_win_E=w.n_win_E, n_win_M=w.n_win_M, overlap_E=w.overlap_E,
-                               overlap_M=w.overlap_M, walkers_per_window=w.walkers_per_window,
+    return oracle.OracleConfig(L=w.L, n_win_E=w.n_win_E, n_win_M=w.n_win_M, overlap_E=w.overlap_E,
+                               overlap_M=w.overlap_M, walkers_per_window=wpw,
                                lnf_init=w.lnf_init, lnf_final=w.lnf_final, lnf_factor=w.lnf_factor,
                                flatness=w.flatness, exchange_interval=w.exchange_interval,
-                               check_every=w.check_every, seed=w.seed(0), drive_budget=10**8)
-    r = oracle.OracleREWL(ocfg)
-    nwalk = r.info()["nwalk"]
+                               check_every=w.check_every, seed=seed, drive_budget=10**8)
+
+
+def _oracle_worker(task):
+    """One host process of the CPU oracle: `warm` untimed cycles, then timed
+    cycles until `steps` cycles or `seconds` of wall time have run; returns
+    (trials timed, seconds timed, cycles timed)."""
+    w, wpw, seed, warm, steps, seconds = task
+    sys.path.insert(0, ROOT)
+    import oracle
+    r = oracle.OracleREWL(_oracle_cfg(w, wpw, seed))
+    live = int(r.windows()[:, 4].sum()) * wpw
+    for _ in range(warm):
+        r.run_cycles(1)
     cyc = 0
     t0 = time.perf_counter()
     while True:
         r.run_cycles(1)
         cyc += 1
         dt = time.perf_counter() - t0
-        if dt >= seconds:
+        if (steps and cyc >= steps) or (not steps and dt >= seconds):
             break
-    trials = cyc * w.exchange_interval * nwalk
     r.close()
-    return {"value": trials / dt, "unit": "trials/s", "cores": 1, "kind": "oracle",
-            "sample": f"{cyc} cycles of {w.name} ({trials} trials) in {dt:.1f} s, single thread"}
+    return cyc * w.exchange_interval * live, dt, cyc
+
+
+def oracle_all_cores(w, seconds: float = 0.0, steps: int = 0, warm: int = 0) -> dict:
+    """The CPU oracle on every host core: one process per core (spawned, so
+    safe after CUDA work), each an independent run of the bounded sample
+    (the workload's geometry, oracle_sample_walkers walkers per window, its
+    own seed); trials/s = all processes' trials / the slowest one's time."""
+    import multiprocessing as mp
+    cores = host_cores()
+    wpw = oracle_sample_walkers(w)
+    tasks = [(w, wpw, w.seed(0) + 7919 * (k + 1), warm, steps, seconds) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, tasks)
+    trials = sum(r[0] for r in res)
+    t = max(r[1] for r in res)
+    cyc = res[0][2]
+    return {"value": trials / t, "unit": "trials/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "seconds": t, "cycles_per_process": cyc,
+            "sample": f"{cores} processes, each an independent run of {w.name} with {wpw} walker(s) per "
+                      f"window (same geometry, {w.exchange_interval} trials per walker per cycle); "
+                      f"{trials} trials in {t:.1f} s"}
 
 
 def run_reference(args, w):
+    """The reference arm: the CPU oracle on every host core.  One step is one
+    cycle of the bounded sample in each process."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    ocfg = oracle.OracleConfig(L=w.L, n_win_E=w.n_win_E, n_win_M=w.n_win_M, overlap_E=w.overlap_E,
-                               overlap_M=w.overlap_M, walkers_per_window=w.walkers_per_window,
-                               lnf_init=w.lnf_init, lnf_final=w.lnf_final, lnf_factor=w.lnf_factor,
-                               flatness=w.flatness, exchange_interval=w.exchange_interval,
-                               check_every=w.check_every, seed=w.seed(0), drive_budget=10**8)
-    r = oracle.OracleREWL(ocfg)
-    nwalk = r.info()["nwalk"]
-    # each step is a bounded sample: one cycle of the workload (one step of the path)
-    for _ in range(args.warmup):
-        r.run_cycles(1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r.run_cycles(1)
-    dt = time.perf_counter() - t0
-    trials = args.steps * w.exchange_interval * nwalk
-    value = trials / dt
+    cb = oracle_all_cores(w, steps=args.steps, warm=args.warmup)
+    value = cb["value"]
     line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": cb["seconds"] / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": _config_dict(w, "none (CPU)"),
-            "cpu_baseline": {"value": value, "unit": "trials/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} cycles of {w.name}, single thread"},
+            "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -356,6 +433,19 @@ def run_eq5(args):
     print(json.dumps(line), flush=True)
 
 
+def warm_run(run, seconds: float, chunk: int) -> dict:
+    """Advances a run through its own cycles (untimed) for `seconds` of wall
+    time, in whole check blocks; returns where it got to."""
+    t0 = time.perf_counter()
+    st = run.status()
+    n = 0
+    while seconds > 0 and not st["done"] and time.perf_counter() - t0 < seconds:
+        st = run.run_cycles(chunk)
+        n += chunk
+    return {"warm_seconds": time.perf_counter() - t0, "cycles_before_timing": st["cycles"],
+            "iteration": st["iteration"], "lnf": st["lnf"], "done": st["done"]}
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -396,7 +486,17 @@ def run_gpu(args, w):
         cfg = autotune(cfg, device=str(dev), samplers=allowed)
     if args.time_to:
         return run_time_to(args, w, cfg, dev)
-    run = P.REWL(cfg, device=str(dev))
+    peaks = None if args.no_peaks else P.measure_peaks(str(dev))
+
+    # the timed state: a restored run, or the run after its own warm-up cycles
+    if args.checkpoint:
+        run = P.REWL.load(args.checkpoint, device=str(dev))
+        st0 = run.status()
+        state = {"checkpoint": os.path.basename(args.checkpoint), "cycles_before_timing": st0["cycles"],
+                 "iteration": st0["iteration"], "lnf": st0["lnf"], "done": st0["done"]}
+    else:
+        run = P.REWL(cfg, device=str(dev))
+        state = warm_run(run, args.warm_seconds, 16 * w.check_every)
     s = run.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     nwalk_active = run.status()["n_walkers"]
@@ -406,6 +506,7 @@ def run_gpu(args, w):
         for _ in range(args.warmup):
             run.enqueue_cycle(sample_part | P.PART_REST)
     s.synchronize()
+    cyc0 = run.status()["cycles"]
 
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
@@ -423,7 +524,7 @@ def run_gpu(args, w):
             ev[k][1].record(s)
             run.enqueue_cycle(P.PART_REST)
             ev[k][2].record(s)
-            check = ((args.warmup + k + 1) % w.check_every) == 0
+            check = ((cyc0 + k + 1) % w.check_every) == 0
             launches += (nwalk_active if plain else 1) + 2 + (2 if check else 0)
     s.synchronize()
     torch.cuda.synchronize()
@@ -435,21 +536,55 @@ def run_gpu(args, w):
     st = run.status()
     value = aggregate_rate(trials_per_step, K, world, total_ms)
 
-    # roofline of the sampling kernel: ALU operations of the method per launch
+    # the plain one-walker-per-launch FP64 form on the same run, continuing its chain
+    plain_line = None
+    if not plain and args.plain_cycles > 0:
+        with torch.cuda.stream(s):
+            run.enqueue_cycle(P.PART_SAMPLE_PLAIN | P.PART_REST)      # untimed: creates its streams
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(args.plain_cycles):
+                run.enqueue_cycle(P.PART_SAMPLE_PLAIN | P.PART_REST)
+            e1.record(s)
+        s.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain_line = {"value": trials_per_step * args.plain_cycles / (pms / 1e3), "unit": "trials/s",
+                      "cycles": args.plain_cycles, "ms_per_step": pms / args.plain_cycles,
+                      "form": "one single-thread launch of k_sweep_thread per walker over 4 streams, "
+                              "host-driven exchange and check, no graph; " + args.precision}
+
+    # roofline of the sampling kernel: the method's operations per launch
+    # against the measured integer-logic issue rate, and its algorithmic
+    # bytes against the measured shared-memory bandwidth
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or 1920.0
-    peak_ops = sm_count * ALU_LANES_PER_SM * mhz * 1e6
     sweep_s = statistics.mean(sweep_ms) / 1e3
     achieved = OPS_PER_TRIAL * trials_per_step / sweep_s
-    kname = "k_sweep_tree" if cfg.sampler == P.SAMPLER_WARP and not plain else "k_sweep_thread"
+    kname = "k_sweep_tree" if cfg.sampler == P.SAMPLER_WARP and not plain and prec != P.F32 else "k_sweep_thread"
     traffic = TRAFFIC.get((w.name, kname, args.precision, sources_hash())) if not plain else None
+    if peaks:
+        peak_ops = peaks["lop3_ops_per_s"]
+        basis = (f"measured on this GPU by rewl_measure_peaks: independent lop3.b32 issue "
+                 f"{peaks['lop3_ops_per_s'] / 1e12:.2f} Tops/s (integer-logic pipe), iadd "
+                 f"{peaks['iadd_ops_per_s'] / 1e12:.2f}, imad {peaks['imad_ops_per_s'] / 1e12:.2f}, ffma "
+                 f"{peaks['ffma_ops_per_s'] / 1e12:.2f} Tops/s, at median SM clock {mhz:.0f} MHz")
+    else:
+        peak_ops = sm_count * ALU_LANES_PER_SM * mhz * 1e6
+        basis = f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x median SM clock {mhz:.0f} MHz (derived)"
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": achieved / peak_ops, "traffic": traffic,
             "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "kernel": kname + (" (one launch per walker, 4 streams)" if plain else ""),
             "kernel_ms_mean": sweep_s * 1e3,
             "kernel_share_of_step": sum(sweep_ms) / total_ms,
-            "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x median SM clock {mhz:.0f} MHz (derived)"}
+            "ops_per_trial": OPS_PER_TRIAL,
+            "peak_basis": basis}
+    if peaks:
+        mem_achieved = BYTES_PER_TRIAL * trials_per_step / sweep_s
+        roof["memory"] = {"bound": "shared memory / L1", "bytes_per_trial": BYTES_PER_TRIAL,
+                          "achieved": mem_achieved / 1e9, "peak": peaks["smem_bytes_per_s"] / 1e9,
+                          "unit": "GB/s", "frac": mem_achieved / peaks["smem_bytes_per_s"],
+                          "l2_peak_gbs": peaks["l2_bytes_per_s"] / 1e9}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -476,18 +611,19 @@ def run_gpu(args, w):
         run2.close()
 
     if rank == 0:
-        cpu = None if args.no_cpu else oracle_rate(w, args.cpu_seconds)
+        cpu = None if args.no_cpu else oracle_all_cores(w, seconds=args.cpu_seconds)
+        state.update({"timed_iteration": st["iteration"], "timed_lnf": st["lnf"]})
         line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.precision],
                 "data": "synthetic",
                 "config": dict(_config_dict(w, "flushed between steps (256 MiB write, outside the step events)",
                                             args.precision, "thread" if plain else _sampler_name(cfg.sampler)),
-                               form=args.form,
+                               form=args.form, state=state,
                                tiling={"sampler": cfg.sampler, "lanes_per_walker": cfg.lanes_per_walker,
                                        "walkers_per_block": cfg.walkers_per_block}),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
-                "clocks": clk,
+                "roofline": roof, "plain": plain_line, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches * world, "clocks": clk, "peaks": peaks,
                 "run": {"iteration": st["iteration"], "lnf": st["lnf"], "exch_accepts": st["exch_accepts"],
                         "exch_attempts": st["exch_attempts"]}}
         print(json.dumps(line), flush=True)
@@ -628,7 +764,7 @@ def run_gpu_batch(args):
     if rank == 0:
         cpu = None
         if not args.no_cpu:
-            cpu = oracle_rate(wl[0], args.cpu_seconds)
+            cpu = oracle_all_cores(wl[0], seconds=args.cpu_seconds)
             cpu["sample"] += " (the L=16 member of the batch, as the per-trial CPU cost)"
         line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,

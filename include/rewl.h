@@ -297,6 +297,28 @@ int rewl_join_noalloc(const rewl_config *cfg, const double *d_lng, const int32_t
                       void *stream);
 const char *rewl_noalloc_last_error(void);
 
+/* Measured rates of the GPU the library runs on (rewl_measure_peaks): the
+ * denominators of the sampling kernels' roofline.  The paper has no
+ * counterpart (it ran on CPUs). */
+typedef struct rewl_peaks {
+    double lop3_ops_per_s;      /* lane operations per second: independent lop3.b32 (integer logic) */
+    double iadd_ops_per_s;      /* independent add.u32 */
+    double imad_ops_per_s;      /* independent mad.lo.u32 */
+    double ffma_ops_per_s;      /* independent fma.rn.f32 */
+    double dep_iadd_cycles;     /* SM cycles per add of one chain of dependent adds */
+    double smem_bytes_per_s;    /* shared-memory read bandwidth of the whole GPU (16-byte loads) */
+    double l2_bytes_per_s;      /* L2 read bandwidth (64 MiB resident, L1 bypassed) */
+    int32_t sms;                /* streaming multiprocessors */
+    int32_t reserved;
+} rewl_peaks;
+/* Runs the microbenchmarks on `stream` (cudaStream_t) and fills *out.
+ * d_scratch: caller-owned device memory, 256-byte aligned, at least 64 MiB +
+ * 4 KiB (the L2 buffer); its contents are overwritten.  Each rate is one
+ * CUDA-event-timed launch after an untimed one; the SM clock is whatever the
+ * GPU runs at meanwhile (sample it beside the call).  Errors: REWL_E_INVALID
+ * (null or short scratch), REWL_E_CUDA. */
+int rewl_measure_peaks(void *d_scratch, size_t scratch_bytes, void *stream, rewl_peaks *out);
+
 /* Relative difference of two density-of-states tables (Eq. 5, Sec. 3:
  * the comparison of a serial WL and a REWL result):
  * d_out[i] = |g_a - g_b| / ((g_a + g_b) / 2) computed from d_lng_a[i] =

@@ -21,7 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librewl.so")
-SOURCES = ["rewl_api.cu", "rewl_kernels.cu", "rewl_sweep_tree.cu", "rewl_join.cu", "rewl_noalloc.cu"]
+SOURCES = ["rewl_api.cu", "rewl_kernels.cu", "rewl_sweep_tree.cu", "rewl_join.cu", "rewl_noalloc.cu", "rewl_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -54,6 +54,13 @@ class rewl_status(ctypes.Structure):
                 ("error", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class rewl_peaks(ctypes.Structure):
+    _fields_ = [("lop3_ops_per_s", ctypes.c_double), ("iadd_ops_per_s", ctypes.c_double),
+                ("imad_ops_per_s", ctypes.c_double), ("ffma_ops_per_s", ctypes.c_double),
+                ("dep_iadd_cycles", ctypes.c_double), ("smem_bytes_per_s", ctypes.c_double),
+                ("l2_bytes_per_s", ctypes.c_double), ("sms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 # Every symbol include/rewl.h declares, with its ctypes signature.
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -88,6 +95,7 @@ SIGNATURES = {
     "rewl_batch_destroy": (ctypes.c_int, [_P]),
     "rewl_join_noalloc": (ctypes.c_int, [ctypes.POINTER(rewl_config), _P, _P, _P, _P]),
     "rewl_noalloc_last_error": (ctypes.c_char_p, []),
+    "rewl_measure_peaks": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.POINTER(rewl_peaks)]),
 }
 
 _lib = None
@@ -365,6 +373,20 @@ def relative_difference(lng_a, lng_b) -> "object":
                                                    ctypes.c_void_p(out.data_ptr()), a.numel(),
                                                    ctypes.c_void_p(s.cuda_stream)))
     return out
+
+
+def measure_peaks(device: str = "cuda:0") -> dict:
+    """Issue and bandwidth rates of the GPU (rewl_measure_peaks), with a
+    64 MiB torch scratch buffer; per second of device time."""
+    import torch
+    dev = torch.device(device)
+    scratch = torch.empty((64 << 20) + 4096, dtype=torch.uint8, device=dev)
+    out = rewl_peaks()
+    s = torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        _check(load_library().rewl_measure_peaks(ctypes.c_void_p(scratch.data_ptr()), scratch.numel(),
+                                                 ctypes.c_void_p(s.cuda_stream), ctypes.byref(out)))
+    return {name: getattr(out, name) for name, _ in rewl_peaks._fields_ if name != "reserved"}
 
 
 class Batch:

@@ -1,6 +1,7 @@
-"""bench.py's reference arm (the CPU oracle) on CPU: one JSON line with the
-keys the benchmark contract names, on the same metric, unit and workload as
-the GPU arm, and a refusal to run the batch workload's ~35 GB of tables."""
+"""bench.py's reference arm (the CPU oracle on every host core) on CPU: one
+JSON line with the keys the benchmark contract names, on the same metric,
+unit and workload as the GPU arm, and a refusal to run the batch workload's
+~35 GB of tables."""
 import json
 import os
 import subprocess
@@ -20,19 +21,25 @@ def _run(*args):
 
 def test_reference_arm_line():
     import bench
+    from paper_1508_02748_gb300 import workloads
     d = _run("--impl", "reference", "--steps", "2", "--warmup", "3")
     assert d["impl"] == "reference"
     assert d["metric"] == bench.METRIC and d["unit"] == "trials/s" and d["higher_is_better"] is True
     assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
-    assert d["config"]["workload"] == "rewl_L8_3x3_w4"
+    assert d["config"]["workload"] == "rewl_L32_16x4_w32"
     assert d["value"] > 0 and d["ms_per_step"] > 0
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    cores = bench.host_cores()
+    assert cb["kind"] == "oracle" and cb["cores"] == cores and cb["value"] == d["value"] and cb["sample"]
+    assert cb["cpu_model"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
-    # 2 cycles x 10^4 trials x 36 walkers in the reported time
-    assert abs(d["value"] * d["ms_per_step"] * 2 / 1e3 - 2 * 10_000 * 36) < 1e-3 * 2 * 10_000 * 36
+    # 2 cycles x 10^4 trials x (64 windows x the sample's walkers) in each process, in the slowest one's time
+    wpw = bench.oracle_sample_walkers(workloads.REWL_L32)
+    assert wpw == 2
+    trials = cores * 2 * 10_000 * 64 * wpw
+    assert abs(d["value"] * d["ms_per_step"] * 2 / 1e3 - trials) < 1e-3 * trials
 
 
 def test_reference_arm_warmup_floor():
