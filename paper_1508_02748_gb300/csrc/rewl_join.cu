@@ -17,6 +17,8 @@
 // of exp/log and of the final parallel normalisation sum.
 #include <math.h>
 
+#include <algorithm>
+
 #include <math_constants.h>
 
 #include "rewl_internal.cuh"
@@ -63,13 +65,41 @@ __device__ double lse_serial(int n, F get)
     return mx + log(acc);
 }
 
-// Matching point (Eq. 4) between marginals Ga, Gb over [lo, hi], p >= floor.
-__device__ int match_point(const double *Ga, const double *Gb, int lo, int hi, int floor_p, double step)
+// Matching point (Eq. 4) between marginals Ga, Gb over [lo, hi], q >= floor:
+// the overlap bin q minimising |beta_a(q) - beta_b(q)|, beta the forward
+// difference over one bin divided by the bin step, taken only where both
+// marginals are finite at q and q + 1; the lowest such q on ties.  Without
+// any, the lowest q where both are finite; -1 if none.
+// It is computed by a whole block (every thread calls it and gets the
+// result): each thread scans a stride of q keeping its first minimum, and
+// the (difference, q) pairs are reduced lexicographically, so the lowest q
+// wins ties.
+constexpr int MATCH_THREADS = 256;
+
+__device__ void block_min_pair(double &d, int &q, double *s_d, int *s_q)
 {
-    int best = -1;
-    double bestd = INFINITY;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xFFFFFFFFu, d, o);
+        const int oq = __shfl_xor_sync(0xFFFFFFFFu, q, o);
+        if (od < d || (od == d && oq < q)) { d = od; q = oq; }
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { s_d[threadIdx.x >> 5] = d; s_q[threadIdx.x >> 5] = q; }
+    __syncthreads();
+    d = s_d[0];
+    q = s_q[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+        if (s_d[k] < d || (s_d[k] == d && s_q[k] < q)) { d = s_d[k]; q = s_q[k]; }
+}
+
+__device__ int match_point_block(const double *Ga, const double *Gb, int lo, int hi, int floor_p, double step)
+{
+    __shared__ double s_d[MATCH_THREADS / 32];
+    __shared__ int s_q[MATCH_THREADS / 32];
     const int start = lo > floor_p ? lo : floor_p;
-    for (int q = start; q + 1 <= hi; ++q) {
+    double bestd = INFINITY;
+    int best = 0x7FFFFFFF;
+    for (int q = start + (int)threadIdx.x; q + 1 <= hi; q += blockDim.x) {
         if (Ga[q] == -INFINITY || Ga[q + 1] == -INFINITY) continue;
         if (Gb[q] == -INFINITY || Gb[q + 1] == -INFINITY) continue;
         const double ba = (Ga[q + 1] - Ga[q]) / step;
@@ -77,10 +107,14 @@ __device__ int match_point(const double *Ga, const double *Gb, int lo, int hi, i
         const double d = fabs(ba - bb);
         if (d < bestd) { bestd = d; best = q; }
     }
-    if (best >= 0) return best;
-    for (int q = start; q <= hi; ++q)
-        if (Ga[q] != -INFINITY && Gb[q] != -INFINITY) return q;
-    return -1;
+    block_min_pair(bestd, best, s_d, s_q);
+    if (best != 0x7FFFFFFF) return best;
+    double z = 0.0;
+    best = 0x7FFFFFFF;
+    for (int q = start + (int)threadIdx.x; q <= hi; q += blockDim.x)
+        if (Ga[q] != -INFINITY && Gb[q] != -INFINITY) { best = q; break; }
+    block_min_pair(z, best, s_d, s_q);
+    return best == 0x7FFFFFFF ? -1 : best;
 }
 
 }  // namespace
@@ -155,42 +189,53 @@ __global__ void k_marg_piece(Params p, JoinScratch j)
     j.GE[idx] = p.active[win] ? lse_serial(p.wM, [&](int i) { return row[i]; }) : -INFINITY;
 }
 
-// 2b. One thread per row b: chain of E matching points along the row.
-__global__ void k_match_e(Params p, JoinScratch j, double *gbuf)
+// 2b. One block per row b: chain of E matching points along the row (the
+// chain is sequential; each matching point and slice rule is block-parallel).
+__global__ void __launch_bounds__(MATCH_THREADS) k_match_e(Params p, JoinScratch j, double *gbuf)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.x;
     if (b >= p.nM) return;
-    const int nE = p.nE, B = p.N + 1;
+    const int nE = p.nE, B = p.N + 1, t0 = threadIdx.x == 0;
     double *Ga = gbuf + (size_t)b * 2 * B, *Gb = Ga + B;
-    for (int a = 0; a < nE; ++a) {
-        j.efrom[b * nE + a] = 0; j.eto[b * nE + a] = 0; j.eshift[b * nE + a] = 0.0;
-        if (a < nE - 1) j.ematch[b * (nE - 1) + a] = -1;
+    __shared__ int s_first, s_last, s_bad;
+    if (t0) {
+        for (int a = 0; a < nE; ++a) {
+            j.efrom[b * nE + a] = 0; j.eto[b * nE + a] = 0; j.eshift[b * nE + a] = 0.0;
+            if (a < nE - 1) j.ematch[b * (nE - 1) + a] = -1;
+        }
+        if (nE == 1) j.ematch[b] = -1;
+        int first = -1, last = -1, bad = 0;
+        for (int a = 0; a < nE; ++a)
+            if (p.active[b * nE + a]) { if (first < 0) first = a; last = a; }
+        j.rowok[b] = first >= 0;
+        for (int a = first; first >= 0 && a <= last; ++a)
+            if (!p.active[b * nE + a]) bad = 1;
+        if (bad) atomicExch(&p.st->join_error, 2);
+        s_first = first; s_last = last; s_bad = bad;
     }
-    if (nE == 1) j.ematch[b] = -1;
-    int first = -1, last = -1;
-    for (int a = 0; a < nE; ++a)
-        if (p.active[b * nE + a]) { if (first < 0) first = a; last = a; }
-    j.rowok[b] = first >= 0;
-    if (first < 0) return;
-    for (int a = first; a <= last; ++a)
-        if (!p.active[b * nE + a]) { atomicExch(&p.st->join_error, 2); return; }
+    __syncthreads();
+    const int first = s_first, last = s_last;
+    if (first < 0 || s_bad) return;
     double shift = 0.0;
     if (p.join_rule == 1)
-        for (int ml = 0; ml < p.wM; ++ml) j.eslice[(size_t)(b * nE + first) * p.wM + ml] = 0.0;
+        for (int ml = threadIdx.x; ml < p.wM; ml += blockDim.x) j.eslice[(size_t)(b * nE + first) * p.wM + ml] = 0.0;
     int from = p.rect[b * nE + first].x;
     for (int a = first; a <= last; ++a) {
         const int A = b * nE + a;
         const int4 RA = p.rect[A];
         int to;
         double next_shift = 0.0;
+        __syncthreads();                      // the last piece's buffers and slices are complete
         if (a < last) {
             const int4 RB = p.rect[A + 1];
-            for (int e = 0; e < B; ++e) { Ga[e] = -INFINITY; Gb[e] = -INFINITY; }
-            for (int e = RA.x; e <= RA.y; ++e) Ga[e] = j.GE[A * p.wE + (e - RA.x)];
-            for (int e = RB.x; e <= RB.y; ++e) Gb[e] = j.GE[(A + 1) * p.wE + (e - RB.x)];
-            const int q = match_point(Ga, Gb, RB.x, RA.y, from, 4.0);
-            if (q < 0) { atomicExch(&p.st->join_error, 3); return; }
-            j.ematch[b * (nE - 1) + a] = q;
+            for (int e = threadIdx.x; e < B; e += blockDim.x) {
+                Ga[e] = (e >= RA.x && e <= RA.y) ? j.GE[A * p.wE + (e - RA.x)] : -INFINITY;
+                Gb[e] = (e >= RB.x && e <= RB.y) ? j.GE[(A + 1) * p.wE + (e - RB.x)] : -INFINITY;
+            }
+            __syncthreads();
+            const int q = match_point_block(Ga, Gb, RB.x, RA.y, from, 4.0);
+            if (q < 0) { if (t0) atomicExch(&p.st->join_error, 3); return; }
+            if (t0) j.ematch[b * (nE - 1) + a] = q;
             next_shift = shift + (Ga[q] - Gb[q]);
             if (p.join_rule == 1) {
                 // the next piece's M slices: each matched at (E_mat, M) where
@@ -199,7 +244,7 @@ __global__ void k_match_e(Params p, JoinScratch j, double *gbuf)
                 const double *pb = j.piece + (size_t)(A + 1) * p.tstride + (size_t)(q - RB.x) * p.wM;
                 const double *sa = j.eslice + (size_t)A * p.wM;
                 double *sb = j.eslice + (size_t)(A + 1) * p.wM;
-                for (int ml = 0; ml < p.wM; ++ml) {
+                for (int ml = threadIdx.x; ml < p.wM; ml += blockDim.x) {
                     const double va = pa[ml], vb = pb[ml];
                     sb[ml] = sa[ml] + ((va != -INFINITY && vb != -INFINITY) ? va - vb : Ga[q] - Gb[q]);
                 }
@@ -208,7 +253,7 @@ __global__ void k_match_e(Params p, JoinScratch j, double *gbuf)
         } else {
             to = RA.y + 1;
         }
-        j.efrom[A] = from; j.eto[A] = to; j.eshift[A] = shift;
+        if (t0) { j.efrom[A] = from; j.eto[A] = to; j.eshift[A] = shift; }
         shift = next_shift;
         from = to;
     }
@@ -241,33 +286,42 @@ __global__ void k_marg_row(Params p, JoinScratch j)
     j.F[idx] = lse_serial(B, [&](int e) { return row_value(p, j, b, e, m); });
 }
 
-// 3b. Single thread: chain of M matching points over the rows.
-__global__ void k_match_m(Params p, JoinScratch j)
+// 3b. One block: chain of M matching points over the rows (sequential
+// chain, block-parallel matching point and slice rule).
+__global__ void __launch_bounds__(MATCH_THREADS) k_match_m(Params p, JoinScratch j)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int nM = p.nM, nE = p.nE, B = p.N + 1;
-    for (int b = 0; b < nM; ++b) { j.mfrom[b] = 0; j.mto[b] = 0; j.mshift[b] = 0.0; }
-    for (int b = 0; b < (nM > 1 ? nM - 1 : 1); ++b) j.mmatch[b] = -1;
-    int first = -1, last = -1;
-    for (int b = 0; b < nM; ++b) if (j.rowok[b]) { if (first < 0) first = b; last = b; }
-    if (first < 0) { atomicExch(&p.st->join_error, 4); return; }
-    for (int b = first; b <= last; ++b) if (!j.rowok[b]) { atomicExch(&p.st->join_error, 5); return; }
+    const int nM = p.nM, nE = p.nE, B = p.N + 1, t0 = threadIdx.x == 0;
+    __shared__ int s_first, s_last, s_bad;
+    if (t0) {
+        for (int b = 0; b < nM; ++b) { j.mfrom[b] = 0; j.mto[b] = 0; j.mshift[b] = 0.0; }
+        for (int b = 0; b < (nM > 1 ? nM - 1 : 1); ++b) j.mmatch[b] = -1;
+        int first = -1, last = -1, bad = 0;
+        for (int b = 0; b < nM; ++b) if (j.rowok[b]) { if (first < 0) first = b; last = b; }
+        if (first < 0) { bad = 1; atomicExch(&p.st->join_error, 4); }
+        for (int b = first; first >= 0 && b <= last; ++b) if (!j.rowok[b]) bad = 1;
+        if (bad && first >= 0) atomicExch(&p.st->join_error, 5);
+        s_first = first; s_last = last; s_bad = bad;
+    }
+    __syncthreads();
+    const int first = s_first, last = s_last;
+    if (s_bad) return;
     double shift = 0.0;
     if (p.join_rule == 1)
-        for (int e = 0; e < B; ++e) j.mslice[(size_t)first * B + e] = 0.0;
+        for (int e = threadIdx.x; e < B; e += blockDim.x) j.mslice[(size_t)first * B + e] = 0.0;
     int from = p.rect[first * nE].z;
     for (int b = first; b <= last; ++b) {
         int to;
         double next_shift = 0.0;
+        __syncthreads();                      // the last row's slices are complete
         if (b < last) {
             const double *Ga = j.F + (size_t)b * B, *Gb = j.F + (size_t)(b + 1) * B;
             const int lo = p.rect[(b + 1) * nE].z, hi = p.rect[b * nE].w;
-            const int q = match_point(Ga, Gb, lo, hi, from, 2.0);
-            if (q < 0) { atomicExch(&p.st->join_error, 6); return; }
-            j.mmatch[b] = q;
+            const int q = match_point_block(Ga, Gb, lo, hi, from, 2.0);
+            if (q < 0) { if (t0) atomicExch(&p.st->join_error, 6); return; }
+            if (t0) j.mmatch[b] = q;
             next_shift = shift + (Ga[q] - Gb[q]);
             if (p.join_rule == 1)
-                for (int e = 0; e < B; ++e) {
+                for (int e = threadIdx.x; e < B; e += blockDim.x) {
                     const double va = row_value(p, j, b, e, q), vb = row_value(p, j, b + 1, e, q);
                     j.mslice[(size_t)(b + 1) * B + e] = j.mslice[(size_t)b * B + e]
                         + ((va != -INFINITY && vb != -INFINITY) ? va - vb : Ga[q] - Gb[q]);
@@ -276,7 +330,7 @@ __global__ void k_match_m(Params p, JoinScratch j)
         } else {
             to = p.rect[b * nE].w + 1;
         }
-        j.mfrom[b] = from; j.mto[b] = to; j.mshift[b] = shift;
+        if (t0) { j.mfrom[b] = from; j.mto[b] = to; j.mshift[b] = shift; }
         shift = next_shift;
         from = to;
     }
@@ -317,10 +371,26 @@ __global__ void k_red_max(const double *v, size_t n, double *red)
     }
 }
 
-__global__ void k_red_sumexp(const double *v, size_t n, const double *red_max, int nblk_max, double *red)
+// Block partials red[0..nblk) folded once, by one block: red[RED_MAX] = the max.
+constexpr int RED_MAX = 1024, RED_SHIFT = 1025;
+
+__global__ void k_red_fold_max(double *red, int nblk)
 {
     double mx = -INFINITY;
-    for (int k = 0; k < nblk_max; ++k) mx = fmax(mx, red_max[k]);
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x) mx = fmax(mx, red[k]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    __shared__ double s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, s[k]);
+        red[RED_MAX] = mx;
+    }
+}
+
+__global__ void k_red_sumexp(const double *v, size_t n, double *red)
+{
+    const double mx = red[RED_MAX];
     double acc = 0.0;
     if (mx != -INFINITY)
         for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -331,17 +401,29 @@ __global__ void k_red_sumexp(const double *v, size_t n, const double *red_max, i
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) acc += s[k];
-        red[blockIdx.x] = acc;
+        red[512 + blockIdx.x] = acc;
     }
 }
 
-__global__ void k_normalise(double *v, size_t n, const double *red_max, const double *red_sum, int nblk, int N)
+// Sum partials red[512..512+nblk) folded in a fixed order; red[RED_SHIFT] =
+// N ln 2 - ln sum g, the shift that makes sum g = 2^N.
+__global__ void k_red_fold_sum(double *red, int nblk, int N)
 {
-    double mx = -INFINITY, acc = 0.0;
-    for (int k = 0; k < nblk; ++k) mx = fmax(mx, red_max[k]);
-    for (int k = 0; k < nblk; ++k) acc += red_sum[k];
-    const double lz = mx + log(acc);
-    const double c = (double)N * log(2.0) - lz;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x) acc += red[512 + k];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    __shared__ double s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) acc += s[k];
+        red[RED_SHIFT] = (double)N * log(2.0) - (red[RED_MAX] + log(acc));
+    }
+}
+
+__global__ void k_normalise(double *v, size_t n, const double *red)
+{
+    const double c = red[RED_SHIFT];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         if (v[i] != -INFINITY) v[i] += c;
 }
@@ -353,15 +435,19 @@ cudaError_t launch_join(const Params &p, const JoinScratch &j, cudaStream_t s)
     const size_t nb = (size_t)p.nwin * p.T;
     k_merge<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(p, j);
     k_marg_piece<<<(p.nwin * p.wE + 127) / 128, 128, 0, s>>>(p, j);
-    k_match_e<<<(p.nM + 31) / 32, 32, 0, s>>>(p, j, j.gbuf);
+    k_match_e<<<p.nM, MATCH_THREADS, 0, s>>>(p, j, j.gbuf);
     k_marg_row<<<(p.nM * B + 127) / 128, 128, 0, s>>>(p, j);
-    k_match_m<<<1, 1, 0, s>>>(p, j);
+    k_match_m<<<1, MATCH_THREADS, 0, s>>>(p, j);
     const size_t nJ = (size_t)B * B;
     k_assemble<<<(unsigned)((nJ + 255) / 256), 256, 0, s>>>(p, j);
-    const int nblk = 512;
+    // normalisation: block maxima, one fold, block sums of exp(v - max), one
+    // fold into the shift, shift applied (grids sized to the table, <= 512)
+    const int nblk = (int)std::min<size_t>(512, (nJ + 255) / 256);
     k_red_max<<<nblk, 256, 0, s>>>(j.J, nJ, j.red);
-    k_red_sumexp<<<nblk, 256, 0, s>>>(j.J, nJ, j.red, nblk, j.red + nblk);
-    k_normalise<<<nblk, 256, 0, s>>>(j.J, nJ, j.red, j.red + nblk, nblk, p.N);
+    k_red_fold_max<<<1, 512, 0, s>>>(j.red, nblk);
+    k_red_sumexp<<<nblk, 256, 0, s>>>(j.J, nJ, j.red);
+    k_red_fold_sum<<<1, 512, 0, s>>>(j.red, nblk, p.N);
+    k_normalise<<<nblk, 256, 0, s>>>(j.J, nJ, j.red);
     return cudaGetLastError();
 }
 

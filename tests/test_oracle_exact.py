@@ -94,8 +94,8 @@ def test_possible_bin_bounds(L):
 
 
 def test_golden_lngE_files_match_closed_form_sums():
-    # ln g(E) for L = 16 (and 32 when present) written by golden/make_golden.py
-    for L in (16, 32):
+    # ln g(E) for L = 16, 32 and 64 written by golden/make_golden.py
+    for L in (16, 32, 64):
         path = os.path.join(GOLD, f"lngE_L{L}.txt")
         if not os.path.exists(path):
             continue
@@ -110,4 +110,6 @@ def test_golden_lngE_files_match_closed_form_sums():
             np.array_equal(np.isinf(v), np.isinf(v[::-1]))
         assert abs(v[0] - math.log(2)) < 1e-12
         assert abs(v[2] - math.log(2 * N)) < 1e-12
+        assert abs(v[3] - math.log(4 * N)) < 1e-12                       # two adjacent flips
+        assert abs(v[4] - math.log(2 * (math.comb(N, 2) + 5 * N))) < 1e-12
         assert np.isinf(v[1]) and np.isinf(v[N - 1])
