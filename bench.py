@@ -122,8 +122,10 @@ def parse():
     ap.add_argument("--form", default="batched", choices=["batched", "plain"],
                     help="plain: each walker's trials as a launch of their own (one thread, 4 streams), "
                          "exchange and check launched from the host, no graph; same trajectory")
-    ap.add_argument("--experiment", default=None, choices=["eq5"],
-                    help="eq5: serial WL vs the paper's REWL split at L = 8, Eq. 5 relative difference")
+    ap.add_argument("--experiment", default=None, choices=["eq5", "precision"],
+                    help="eq5: serial WL vs the paper's REWL split at L = 8, Eq. 5 relative difference; "
+                         "precision: the L = 64 precision study (FP64, f32x2, plain float)")
+    ap.add_argument("--late-cycles", type=int, default=8, help="--experiment precision: cycles from the late state")
     ap.add_argument("--time-to", action="store_true",
                     help="run the workload to its final ln f and report the wall time and ln g error")
     return ap.parse_args()
@@ -586,28 +588,30 @@ def run_gpu(args, w):
                           "unit": "GB/s", "frac": mem_achieved / peaks["smem_bytes_per_s"],
                           "l2_peak_gbs": peaks["l2_bytes_per_s"] / 1e9}
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: the run created from
+    # host spin bytes, K synchronous steps each reading the run status back,
+    # then every walker's state (e, m, trials, flat verdict) copied to host
+    # memory as the result (the joined table needs every window overlap
+    # visited, which a run this young may not have)
     e2e = None
     if not args.no_e2e:
         rng = np.random.default_rng(w.seed(rank) + 7)
         host_spins = rng.integers(0, 2, size=(w.n_walkers, w.N), dtype=np.uint8)
         pinned = torch.from_numpy(host_spins).pin_memory().numpy()
-        out = np.empty((w.N + 1) * (w.N + 1), dtype=np.float64)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         run2 = P.REWL(cfg, init_spins=pinned, device=str(dev), stream=s)
         for _ in range(K):
             (run2.run_cycles_plain if plain else run2.run_cycles)(1)
-        J = run2.lng()
+        states, _ = run2.walkers(spins=False)
         t1 = time.perf_counter()
-        out[:] = J.ravel()
         e2e_trials = trials_per_step * K
         status_bytes = 64
         e2e = {"value": e2e_trials * world / (t1 - t0), "unit": "trials/s",
                "h2d_bytes_per_step": (host_spins.nbytes + 128) / K,
-               "d2h_bytes_per_step": status_bytes + out.nbytes / K,
+               "d2h_bytes_per_step": status_bytes + states.nbytes / K,
                "includes": "create from host spins + drive, K synchronous steps with status readback, "
-                           "join + normalise + joined table to host"}
+                           "walker states to host"}
         run2.close()
 
     if rank == 0:
@@ -676,6 +680,101 @@ def run_time_to(args, w, cfg, dev):
     run.close()
 
 
+def run_precision(args):
+    """The precision study of the L = 64 workload (32 x 8 windows at 75%
+    overlap, 16 walkers per window, ln f halved from 1 down to 1e-8), one GPU.
+
+    A: from creation, the FP64 run advances --max-seconds of wall time; the
+       compensated-pair (f32x2) and plain-float runs do the same number of
+       cycles from the same seed.  Their tables are compared by the device
+       digest of every walker's ln g and H; the joined E marginal's error
+       against the exact g(E) is given where every window overlap has been
+       visited (else null).
+    B: a late state at the finest ln f of the study, 2^-27: every bin of the
+       one-walker-per-window geometry at ln g = 2^14 plus up to 2^-7 in steps
+       of 2^-27, H = 0; --late-cycles cycles in each format, then each
+       visited entry's gain is compared with its visits x ln f exactly."""
+    import numpy as np
+    import torch
+
+    import paper_1508_02748_gb300 as P
+    from paper_1508_02748_gb300 import build as pkg_build
+
+    pkg_build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = workloads.REWL_L64
+    fmt = {"fp64": P.FP64, "f32x2": P.F32X2, "f32": P.F32}
+    ex = exact_lngE(64)
+    out = {"A": {}, "B": {}}
+    cycles = None
+    for name in ("fp64", "f32x2", "f32"):
+        cfg = P.Config.from_workload(w, replicate=args.replicate, drive_budget=10**8, precision=fmt[name])
+        run = P.REWL(cfg, device=str(dev))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = run.status()
+        if cycles is None:
+            while time.perf_counter() - t0 < args.max_seconds and not st["done"]:
+                st = run.run_cycles(16 * w.check_every)
+            cycles = st["cycles"]
+        else:
+            st = run.run_cycles(cycles)
+        dt = time.perf_counter() - t0
+        eps = None
+        try:
+            mE = run.lng(P.LNG_MARGINAL_E)
+            ok = np.isfinite(ex) & (ex > 0) & np.isfinite(mE)
+            eps = float(np.mean(np.abs(mE[ok] - ex[ok]) / ex[ok]))
+        except P.REWLError as e:
+            eps = f"not joinable yet: {e}"
+        out["A"][name] = {"cycles": st["cycles"], "iteration": st["iteration"], "lnf": st["lnf"],
+                          "seconds": dt, "trials_per_s": st["cycles"] * w.exchange_interval * st["n_walkers"] / dt,
+                          "digest": f"{run.digest():016x}", "mean_eps_E_marginal_vs_exact": eps}
+        run.close()
+        del run
+        torch.cuda.empty_cache()
+    A = out["A"]
+    out["A"]["f32x2_equals_fp64"] = A["f32x2"]["digest"] == A["fp64"]["digest"]
+    out["A"]["f32_equals_fp64"] = A["f32"]["digest"] == A["fp64"]["digest"]
+
+    rng = np.random.default_rng(11)
+    base = H0 = None
+    tabs = {}
+    for name in ("fp64", "f32x2", "f32"):
+        cfg = P.Config.from_workload(w.with_(walkers_per_window=1, lnf_init=2.0 ** -27), replicate=args.replicate,
+                                     drive_budget=10**8, precision=fmt[name])
+        run = P.REWL(cfg, device=str(dev))
+        if base is None:
+            n = run.tables()[1].size
+            base = 16384 + rng.integers(0, 2**20, size=n) * 2.0 ** -27
+            H0 = np.zeros(n, dtype=np.int32)
+        run.set_tables(base, H0)
+        run.run_cycles(args.late_cycles)
+        lng, H = run.tables()
+        vis = H > 0
+        stored = base if name != "f32" else base.astype(np.float32).astype(np.float64)
+        gain = lng[vis] - stored[vis]
+        want = H[vis] * 2.0 ** -27
+        out["B"][name] = {"visited_entries": int(vis.sum()), "visits": int(H.sum()),
+                          "entries_gaining_exactly_visits_x_lnf": int((gain == want).sum()),
+                          "entries_gaining_nothing": int((gain == 0).sum()),
+                          "lost_lng_total": float((want - gain).sum()), "digest": f"{run.digest():016x}"}
+        tabs[name] = lng
+        run.close()
+        del run
+        torch.cuda.empty_cache()
+    out["B"]["f32x2_equals_fp64"] = bool(np.array_equal(tabs["f32x2"], tabs["fp64"]))
+    line = {"metric": "precision study: ln g tables of the exact formats and plain float", "value":
+            float(out["A"]["f32x2_equals_fp64"] and out["B"]["f32x2_equals_fp64"]), "unit": "1 = f32x2 equals FP64",
+            "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": w.name, "L": 64, "windows": "32x8", "walkers_per_window": 16,
+                       "max_seconds": args.max_seconds, "late_cycles": args.late_cycles,
+                       "late_state": "one walker per window, ln g = 2^14 + U{0..2^20} 2^-27, H = 0, ln f = 2^-27"},
+            "runs": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu_batch(args):
     """The uneven batch: 24 runs of L = 16, 24, 32, 48 advanced together by
     one CUDA graph per step (K = 8 cycles of every run)."""
@@ -704,9 +803,11 @@ def run_gpu_batch(args):
         return rs, P.Batch(rs)
 
     choices = []
-    if args.sampler in ("auto", "warp"):
+    if args.lanes is not None:
+        choices = [(P.SAMPLER_WARP, args.lanes, args.wpb or 0)]
+    elif args.sampler in ("auto", "warp"):
         choices += [(P.SAMPLER_WARP, lanes, 0) for lanes in (32, 16, 8)]
-    if args.sampler in ("auto", "thread"):
+    if args.lanes is None and args.sampler in ("auto", "thread"):
         choices += [(P.SAMPLER_THREAD, 0, wpb) for wpb in (32, 64)]
     best, tune = choices[0], {}
     if not args.no_autotune and len(choices) > 1:
@@ -801,6 +902,9 @@ def main():
     if args.experiment == "eq5":
         args.precision = args.precision or "fp64"
         run_eq5(args)
+        return
+    if args.experiment == "precision":
+        run_precision(args)
         return
     if args.workload == workloads.BATCH_NAME:
         if args.precision is None or args.precision == "fp64":

@@ -206,6 +206,13 @@ int rewl_get_tables(rewl_t *h, double *host_lng, int32_t *host_H, size_t capacit
  * decides with.  count must equal the number of entries get returns. */
 int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t *host_H, size_t count);
 
+/* Order-independent 64-bit digest of every walker's tables on the device:
+ * the bit patterns of each entry's ln g (as rewl_get_tables gives it) and H,
+ * mixed with the entry's index and summed modulo 2^64.  Runs whose tables
+ * hold the same values have the same digest whatever their format; used to
+ * compare table sets too large to copy to the host. */
+int rewl_tables_digest(rewl_t *h, uint64_t *digest);
+
 /* Final merge of each window's walkers, join (Eqs. 3-4, E then M) and
  * normalisation to sum g = 2^N, all on the device, copied to host_out.
  * what = REWL_LNG_JOINED or REWL_LNG_MARGINAL_E, optionally OR

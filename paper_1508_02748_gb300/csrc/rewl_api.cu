@@ -907,6 +907,19 @@ extern "C" int rewl_set_tables(rewl_t *h, const double *host_lng, const int32_t 
     return sync(h);
 }
 
+extern "C" int rewl_tables_digest(rewl_t *h, uint64_t *digest)
+{
+    if (!h || !digest) return REWL_E_INVALID;
+    unsigned long long *d = (unsigned long long *)h->d_stage;   // the staging area is free between calls
+    CK(h, cudaMemsetAsync(d, 0, 8, h->stream));
+    CK(h, launch_digest(h->p, d, h->stream));
+    unsigned long long v = 0;
+    CK(h, cudaMemcpyAsync(&v, d, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *digest = v;
+    return REWL_OK;
+}
+
 extern "C" int rewl_get_lng(rewl_t *h, int what, double *host_out, size_t capacity, size_t *needed,
                             int32_t *host_ematch, int32_t *host_mmatch)
 {

@@ -144,6 +144,7 @@ cudaError_t launch_decide(const Params &p, int flags, cudaStream_t s);
 // base += H * lnf_done and H -> 0 on visited bins; the screens are refreshed
 // in both cases (fold = 0: after the tables were written from the host).
 cudaError_t launch_fold(const Params &p, int fold, cudaStream_t s);
+cudaError_t launch_digest(const Params &p, unsigned long long *d_out, cudaStream_t s);
 cudaError_t launch_rel_diff(const double *a, const double *b, double *out, size_t n, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *d_ctr, uint32_t k0, uint32_t k1, uint32_t *d_out,
                           uint64_t n, cudaStream_t s);

@@ -604,6 +604,40 @@ cudaError_t launch_fold(const Params &p, int fold, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Order-independent digest of every walker's tables: for each entry, the bit
+// pattern of its ln g as a double (base + max(H, 0) ln f in the exact
+// formats) and its H are mixed with the entry's index by a 64-bit finaliser
+// (the multiply-xorshift steps of splitmix64) and summed modulo 2^64, so two
+// runs have equal digests when their tables hold the same values.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_digest(Params p, unsigned long long *out)
+{
+    const size_t n = (size_t)p.nwalk * p.T;
+    const double lnf = p.st->lnf;
+    unsigned long long acc = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = i / p.T, b = i % p.T;
+        const size_t q = w * p.tstride + b;
+        const double v = lng_read(p, q, lnf);
+        const unsigned long long h = (unsigned long long)(uint32_t)p.H[q];
+        acc += mix64((unsigned long long)__double_as_longlong(v) ^ mix64(i)) + mix64(h + 0x9E3779B97F4A7C15ull * i);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+cudaError_t launch_digest(const Params &p, unsigned long long *d_out, cudaStream_t s)
+{
+    k_digest<<<1024, 256, 0, s>>>(p, d_out);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- philox ----
 
 __global__ void k_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, uint64_t n)

@@ -22,12 +22,15 @@
 //      ln f.
 // One ballot gives the true path from the root: a lane is on it iff the
 // ballot bits of its ancestors are the outcomes its history assumes.  Lane k
-// of the path posts the position after trial t+k (and, for a register
-// lattice, the site it flipped) in a per-walker mailbox in shared memory;
-// after one warp barrier every lane knows the path, and the shallowest path
-// lane that ends in each bin the walker leaves writes that bin's new visit
-// count H.  The leaf also posts the count and screen value of the final bin,
-// so the group adopts its new state without another table read.
+// of the path knows how often its bin was visited on the path up to trial
+// t+k (its own history's count plus one), so it writes that bin's H as the
+// count it had plus those visits; the lanes write in path order (one store
+// per depth, warp barriers between), so a bin visited again later ends with
+// the larger count.  The leaf posts the final position, its visits on the
+// path, its H and its screen value in a per-walker mailbox in shared memory
+// (a register lattice also gets the path's flipped sites there), so the
+// group adopts its new state without comparing the path's bins or reading
+// the table again.
 //
 // Tables (exact formats only; REWL_F32 runs on the thread sampler): ln g(b)
 // = base(b) + max(H(b), 0) ln f, the base fixed during an iteration, so a
@@ -85,11 +88,11 @@ struct RingEntry {
 
 // Per-walker exchange area of one step (shared memory).
 struct Mailbox {
-    int after[8];                  // position e << 16 | m after trial t+k on the true path
     int fsite[8];                  // register lattice: bit index flipped by trial t+k, 64 if none
-    int leafq;                     // H of the final bin as read this step (>= 0)
+    int leafC;                     // position e << 16 | m after the last trial
+    int leafcC;                    // the path's visits of that bin
+    int leafq;                     // its H as read this step (>= 0)
     float leafs;                   // its screen value
-    int pad[2];
 };
 
 // Eq. 1 decided from the exact values (near-ties of the float screen only);
@@ -362,28 +365,36 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         const unsigned bal = (__ballot_sync(gmask, acc) >> (grp * G)) & GBITS;
         const bool onp = dl <= D && ((bal ^ want) & anc) == 0u;
 
-        // ---- commit: the on-path lane of depth k takes trial t+k
+        // ---- commit: the on-path lane of depth k takes trial t+k.  Its bin has
+        // cupto path visits up to and including this trial, so its H becomes
+        // cupto plus the H it had (the current bin: lq).
         const int aq = acc ? hn : hc;             // H of `after` as read (unless it is the current bin)
+        const int cupto = (acc ? vnew : vcur) + 1;
+        const int val = cupto + (after == P0 ? lq : aq);
+        const unsigned aidx = acc ? nu : cu;
         if (onp) {
-            box->after[dl] = after;
             if (REG) box->fsite[dl] = acc ? (int)(me.a & 63u) : 64;
             if (dl == D) {
+                box->leafC = after;
+                box->leafcC = cupto;
                 box->leafq = aq;
                 box->leafs = acc ? ns : cs;
             }
+            err |= val < 0;
         }
-        __syncwarp(gmask);
-        int av[DEPTH + 1];
-        #pragma unroll
-        for (int k = 0; k <= DEPTH; ++k) av[k] = k <= D ? box->after[k] : -1;
-        const int C = box->after[D];
-        int cC = 0;
-        bool b0_seen = false;
+        // H of the bins visited in this step, in path order: the pending count of
+        // the start bin, then each trial's bin with its visits so far; a bin
+        // visited again later in the step is overwritten with the larger count,
+        // so every bin ends with all its visits (the warp barriers order the
+        // stores of different lanes to one address)
+        if (gl == 0 && hq > 0) Hh[ci] = lq;
         #pragma unroll
         for (int k = 0; k <= DEPTH; ++k) {
-            cC += (av[k] == C);
-            b0_seen |= (av[k] == P0);
+            __syncwarp(gmask);
+            if (onp && dl == k) Hh[aidx] = val;
         }
+        __syncwarp(gmask);
+        const int C = box->leafC, cC = box->leafcC;
         if (REG) {
             #pragma unroll
             for (int k = 0; k <= DEPTH; ++k) {
@@ -396,31 +407,10 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             const uint32_t fi = me.a & 63u, fj = (me.a >> 6) & 63u;
             atomicXor(&lat[fi * WPR + ((WPR == 1) ? 0 : (fj >> 5))], 1u << (fj & 31));
         }
-        // write-back of the bins the walker leaves in this step: the shallowest
-        // on-path lane that ended in such a bin writes its H with all its visits
-        // of the step; lane G-1 (never on the path) writes the start bin when
-        // it is left without being visited again
-        {
-            bool firstv = true;
-            int cntv = 0;
-            #pragma unroll
-            for (int k = 0; k <= DEPTH; ++k) {
-                if (k < dl && av[k] == after) firstv = false;
-                cntv += (av[k] == after);
-            }
-            const bool own = onp && firstv && after != C;
-            const bool entry_left = gl == G - 1 && C != P0 && !b0_seen && hq > 0;
-            const unsigned aidx = acc ? nu : cu;
-            const int val = own ? cntv + (after == P0 ? lq : aq) : lq;
-            if (own || entry_left) {
-                Hh[own ? aidx : (unsigned)ci] = val;
-                err |= val < 0;
-            }
-        }
         // the group adopts the state after the last trial
         {
             const bool same = C == P0;
-            const int nlq = same ? lq + cC : box->leafq + cC;
+            const int nlq = (same ? lq : box->leafq) + cC;
             const float ns32 = box->leafs;
             hq = same ? hq + cC : cC;
             lq = nlq;

@@ -78,6 +78,7 @@ SIGNATURES = {
     "rewl_get_walkers": (ctypes.c_int, [_P, _P, _P]),
     "rewl_get_tables": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t]),
     "rewl_set_tables": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t]),
+    "rewl_tables_digest": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "rewl_get_lng": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _P, _P]),
     "rewl_get_lng_jackknife": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_size_t,
                                               ctypes.POINTER(ctypes.c_size_t)]),
@@ -269,6 +270,12 @@ class REWL:
         lng = np.ascontiguousarray(lng, dtype=np.float64)
         H = np.ascontiguousarray(H, dtype=np.int32)
         _check(load_library().rewl_set_tables(self._h, lng.ctypes.data, H.ctypes.data, lng.size), self._h)
+
+    def digest(self) -> int:
+        """Order-independent digest of every walker's ln g and H (rewl_tables_digest)."""
+        d = ctypes.c_uint64(0)
+        _check(load_library().rewl_tables_digest(self._h, ctypes.byref(d)), self._h)
+        return int(d.value)
 
     def lng(self, what: int = LNG_JOINED, matches: bool = False, rule: int = JOIN_MARGINAL):
         """Joined ln g (or its E marginal); rule JOIN_PER_SLICE rescales each
