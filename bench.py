@@ -66,13 +66,24 @@ OPS_PER_TRIAL = 120
 # written 16 B).
 BYTES_PER_TRIAL = 40
 
-# DRAM bytes (read + write) per launch of the sampling kernel from one ncu
-# capture (the profiles directory has the capture's summary), keyed by
-# workload, kernel and table format, valid only for the kernel sources they
-# were taken on (hash of the files below); any other case reports null.
+# Counters of the sampling kernel from ncu captures (their summaries are in
+# the profiles directory), per launch in the benchmark's launch
+# configuration, keyed by workload, kernel, table format, lanes per walker
+# and the hash of the kernel sources (any other case reports null):
+# dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum of one launch;
+# warp_inst_per_trial = smsp__inst_executed.sum / trials of one launch.
 TRAFFIC_SOURCES = ("paper_1508_02748_gb300/csrc/rewl_sweep_tree.cu", "paper_1508_02748_gb300/csrc/rewl_tab.cuh",
                    "paper_1508_02748_gb300/csrc/rewl_internal.cuh")
-TRAFFIC = {("rewl_L8_3x3_w4", "k_sweep_tree", "fp64", "ae409ff7080ec0e0"): 845568 + 0}
+PROFILE = {
+    # L = 32, 16 x 4 windows, 32 walkers each, 32 lanes per walker: DRAM bytes from a one-pass capture
+    # of the full workload after 512 warm-up cycles; instructions per trial from the full capture of
+    # the same kernel at 16 walkers per window
+    ("rewl_L32_16x4_w32", "k_sweep_tree", "fp64", 32, "a08a3138e84675cd"): {"dram_bytes": 142_710_000,
+                                                               "warp_inst_per_trial": 53.22},
+    # L = 8, 3 x 3 windows, 4 walkers each, 32 lanes per walker (tables staged in shared memory)
+    ("rewl_L8_3x3_w4", "k_sweep_tree", "fp64", 32, "a08a3138e84675cd"): {"dram_bytes": 607_488,
+                                                            "warp_inst_per_trial": 61.30},
+}
 
 
 def sources_hash() -> str:
@@ -97,8 +108,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the peak microbenchmarks (derived ALU peak)")
+    ap.add_argument("--no-time-to", action="store_true",
+                    help="skip the time-to-ln f <= 1e-6 run of the L = 8 workload added to the line")
     ap.add_argument("--warm-seconds", type=float, default=20.0,
                     help="untimed cycles of the run itself before the timed ones (wall seconds)")
+    ap.add_argument("--warm-cycles", type=int, default=None,
+                    help="untimed cycles of the run itself before the timed ones (a cycle count; replaces "
+                         "--warm-seconds, for profiler captures that skip to a fixed launch)")
     ap.add_argument("--checkpoint", default=None, help="time a run restored from this checkpoint (rewl_save)")
     ap.add_argument("--plain-cycles", type=int, default=1,
                     help="cycles of the plain one-walker-per-launch form timed after the batched ones (0: skip)")
@@ -435,15 +451,18 @@ def run_eq5(args):
     print(json.dumps(line), flush=True)
 
 
-def warm_run(run, seconds: float, chunk: int) -> dict:
-    """Advances a run through its own cycles (untimed) for `seconds` of wall
-    time, in whole check blocks; returns where it got to."""
+def warm_run(run, seconds: float, chunk: int, cycles: int | None = None) -> dict:
+    """Advances a run through its own cycles (untimed): exactly `cycles`
+    cycles when given, else whole check blocks for `seconds` of wall time;
+    returns where it got to."""
     t0 = time.perf_counter()
     st = run.status()
-    n = 0
+    if cycles is not None:
+        if cycles > 0:
+            st = run.run_cycles(cycles)
+        seconds = 0
     while seconds > 0 and not st["done"] and time.perf_counter() - t0 < seconds:
         st = run.run_cycles(chunk)
-        n += chunk
     return {"warm_seconds": time.perf_counter() - t0, "cycles_before_timing": st["cycles"],
             "iteration": st["iteration"], "lnf": st["lnf"], "done": st["done"]}
 
@@ -498,7 +517,7 @@ def run_gpu(args, w):
                  "iteration": st0["iteration"], "lnf": st0["lnf"], "done": st0["done"]}
     else:
         run = P.REWL(cfg, device=str(dev))
-        state = warm_run(run, args.warm_seconds, 16 * w.check_every)
+        state = warm_run(run, args.warm_seconds, 16 * w.check_every, args.warm_cycles)
     s = run.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     nwalk_active = run.status()["n_walkers"]
@@ -563,7 +582,8 @@ def run_gpu(args, w):
     sweep_s = statistics.mean(sweep_ms) / 1e3
     achieved = OPS_PER_TRIAL * trials_per_step / sweep_s
     kname = "k_sweep_tree" if cfg.sampler == P.SAMPLER_WARP and not plain and prec != P.F32 else "k_sweep_thread"
-    traffic = TRAFFIC.get((w.name, kname, args.precision, sources_hash())) if not plain else None
+    prof = PROFILE.get((w.name, kname, args.precision, cfg.lanes_per_walker, sources_hash())) if not plain else None
+    traffic = prof["dram_bytes"] if prof else None
     if peaks:
         peak_ops = peaks["lop3_ops_per_s"]
         basis = (f"measured on this GPU by rewl_measure_peaks: independent lop3.b32 issue "
@@ -581,6 +601,15 @@ def run_gpu(args, w):
             "kernel_share_of_step": sum(sweep_ms) / total_ms,
             "ops_per_trial": OPS_PER_TRIAL,
             "peak_basis": basis}
+    if peaks and prof:
+        # instruction issue: the kernel's measured instructions per trial at the
+        # live trial rate against one warp instruction per cycle per SM
+        # sub-partition (the independent-add stream of rewl_measure_peaks)
+        lane_inst = prof["warp_inst_per_trial"] * 32
+        roof["issue"] = {"lane_instructions_per_trial": lane_inst, "algorithmic_ops_per_trial": OPS_PER_TRIAL,
+                         "achieved": lane_inst * trials_per_step / sweep_s / 1e12,
+                         "peak": peaks["iadd_ops_per_s"] / 1e12, "unit": "Tlane-instructions/s",
+                         "frac": lane_inst * trials_per_step / sweep_s / peaks["iadd_ops_per_s"]}
     if peaks:
         mem_achieved = BYTES_PER_TRIAL * trials_per_step / sweep_s
         roof["memory"] = {"bound": "shared memory / L1", "bytes_per_trial": BYTES_PER_TRIAL,
@@ -614,6 +643,10 @@ def run_gpu(args, w):
                            "walker states to host"}
         run2.close()
 
+    tt = None
+    if rank == 0 and not args.no_time_to:
+        tt = time_to_line(args, dev)
+
     if rank == 0:
         cpu = None if args.no_cpu else oracle_all_cores(w, seconds=args.cpu_seconds)
         state.update({"timed_iteration": st["iteration"], "timed_lnf": st["lnf"]})
@@ -626,7 +659,7 @@ def run_gpu(args, w):
                                form=args.form, state=state,
                                tiling={"sampler": cfg.sampler, "lanes_per_walker": cfg.lanes_per_walker,
                                        "walkers_per_block": cfg.walkers_per_block}),
-                "roofline": roof, "plain": plain_line, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "plain": plain_line, "time_to": tt, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * world, "clocks": clk, "peaks": peaks,
                 "run": {"iteration": st["iteration"], "lnf": st["lnf"], "exch_accepts": st["exch_accepts"],
                         "exch_attempts": st["exch_attempts"]}}
@@ -635,6 +668,57 @@ def run_gpu(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def time_to_line(args, dev) -> dict:
+    """The metric's time-to half on the workload where a run reaches its final
+    ln f inside a benchmark: 2D REWL at L = 8 (3 x 3 windows, 4 walkers per
+    window), FP64, batched, run from creation to ln f <= 1e-6; the plain
+    one-walker-per-launch form follows the same chain (same cycles, same
+    tables), so its wall time is its measured time per cycle on this workload
+    times the batched run's cycles (labelled extrapolated)."""
+    import numpy as np
+    import torch
+
+    import paper_1508_02748_gb300 as P
+    w = workloads.REWL_L8
+    cfg = P.Config.from_workload(w, replicate=args.replicate, drive_budget=10**8, precision=P.FP64,
+                                 lanes_per_walker=32, walkers_per_block=2)
+    run = P.REWL(cfg, device=str(dev))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = run.status()
+    while not st["done"] and time.perf_counter() - t0 < args.max_seconds:
+        st = run.run_cycles(64)
+    elapsed = time.perf_counter() - t0
+    eps = None
+    if st["done"]:
+        mE = run.lng(P.LNG_MARGINAL_E)
+        ex = exact_lngE(w.L)
+        ok = np.isfinite(ex) & (ex > 0) & np.isfinite(mE)
+        eps = float(np.mean(np.abs(mE[ok] - ex[ok]) / ex[ok]))
+    run.close()
+    # the plain form's time per cycle on the same workload (a fresh run, 24 cycles after 2)
+    pr = P.REWL(cfg, device=str(dev))
+    s = pr.stream
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            pr.enqueue_cycle(P.PART_SAMPLE_PLAIN | P.PART_REST)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(24):
+            pr.enqueue_cycle(P.PART_SAMPLE_PLAIN | P.PART_REST)
+        e1.record(s)
+    s.synchronize()
+    plain_ms = e0.elapsed_time(e1) / 24
+    pr.close()
+    return {"workload": w.name, "seed": cfg.seed, "final_lnf": st["lnf"], "done": bool(st["done"]),
+            "iterations": st["iteration"], "cycles": st["cycles"],
+            "batched_fp64_seconds": elapsed, "mean_eps_E_marginal_vs_exact": eps,
+            "plain_fp64_ms_per_cycle": plain_ms,
+            "plain_fp64_seconds_extrapolated": plain_ms * st["cycles"] / 1e3,
+            "note": "plain = same chain (bit for bit), so the same cycles and the same tables; its wall time is "
+                    "its measured ms per cycle times those cycles"}
 
 
 def run_time_to(args, w, cfg, dev):
