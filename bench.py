@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the peak microbenchmarks (derived ALU peak)")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the short timings of the L = 64 workload and the uneven batch added to the line")
     ap.add_argument("--no-time-to", action="store_true",
                     help="skip the time-to-ln f <= 1e-6 run of the L = 8 workload added to the line")
     ap.add_argument("--warm-seconds", type=float, default=20.0,
@@ -646,6 +648,9 @@ def run_gpu(args, w):
     tt = None
     if rank == 0 and not args.no_time_to:
         tt = time_to_line(args, dev)
+    others = None
+    if rank == 0 and not args.no_others and w.name == workloads.REWL_L32.name:
+        others = other_workloads_line(args, dev)
 
     if rank == 0:
         cpu = None if args.no_cpu else oracle_all_cores(w, seconds=args.cpu_seconds)
@@ -659,7 +664,7 @@ def run_gpu(args, w):
                                form=args.form, state=state,
                                tiling={"sampler": cfg.sampler, "lanes_per_walker": cfg.lanes_per_walker,
                                        "walkers_per_block": cfg.walkers_per_block}),
-                "roofline": roof, "plain": plain_line, "time_to": tt, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "plain": plain_line, "time_to": tt, "others": others, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * world, "clocks": clk, "peaks": peaks,
                 "run": {"iteration": st["iteration"], "lnf": st["lnf"], "exch_accepts": st["exch_accepts"],
                         "exch_attempts": st["exch_attempts"]}}
@@ -668,6 +673,71 @@ def run_gpu(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def other_workloads_line(args, dev) -> dict:
+    """Short device-timed runs of the other workloads the metric is quoted
+    on, in the same line: the L = 64 precision-study geometry (32 x 8
+    windows, 16 walkers per window, FP64, 16 lanes per walker) after 10 s
+    of its own cycles, 20 timed cycles; and the uneven batch of 24 runs
+    (L = 16, 24, 32, 48; compensated f32; 16 lanes), 5 timed graph launches
+    of 8 cycles.  L2 flushed between steps; CUDA events on the run's stream."""
+    import torch
+
+    import paper_1508_02748_gb300 as P
+    out = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(stream, n, enqueue):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        with torch.cuda.stream(stream):
+            for k in range(n):
+                flush.zero_()
+                ev[k][0].record(stream)
+                enqueue()
+                ev[k][1].record(stream)
+        stream.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / n
+
+    try:
+        w = workloads.REWL_L64
+        cfg = P.Config.from_workload(w, replicate=args.replicate, drive_budget=10**8, precision=P.FP64,
+                                     lanes_per_walker=16, walkers_per_block=1)
+        run = P.REWL(cfg, device=str(dev))
+        state = warm_run(run, 10.0, 16 * w.check_every)
+        nw = run.status()["n_walkers"]
+        ms = timed(run.stream, 20, lambda: run.enqueue_cycle(P.PART_SAMPLE | P.PART_REST))
+        st = run.status()
+        out[w.name] = {"value": w.exchange_interval * nw / (ms / 1e3), "unit": "trials/s", "ms_per_step": ms,
+                       "steps": 20, "ln_g": "fp64", "lanes_per_walker": 16, "walkers": nw,
+                       "state": dict(state, timed_iteration=st["iteration"], timed_lnf=st["lnf"])}
+        run.close()
+        del run
+        torch.cuda.empty_cache()
+    except Exception as e:                      # noqa: BLE001 -- reported in the line
+        out[workloads.REWL_L64.name] = {"error": str(e)}
+    try:
+        wl = workloads.mixed_batch()
+        runs = [P.REWL(P.Config.from_workload(w, replicate=i, drive_budget=10**8, precision=P.F32X2,
+                                              lanes_per_walker=16), device=str(dev)) for i, w in enumerate(wl)]
+        b = P.Batch(runs)
+        with torch.cuda.stream(b.stream):
+            for _ in range(3):
+                b.enqueue()
+        b.stream.synchronize()
+        ms = timed(b.stream, 5, b.enqueue)
+        active = sum(r.status()["n_walkers"] for r in runs)
+        out[workloads.BATCH_NAME] = {"value": b.k * wl[0].exchange_interval * active / (ms / 1e3), "unit": "trials/s",
+                                     "ms_per_step": ms, "cycles_per_step": b.k, "steps": 5, "ln_g": "f32x2",
+                                     "lanes_per_walker": 16, "walkers": active, "runs": len(runs)}
+        b.close()
+        for r in runs:
+            r.close()
+        del runs, b
+        torch.cuda.empty_cache()
+    except Exception as e:                      # noqa: BLE001 -- reported in the line
+        out[workloads.BATCH_NAME] = {"error": str(e)}
+    return out
 
 
 def time_to_line(args, dev) -> dict:
