@@ -64,6 +64,13 @@ extern "C" {
                                    below half an ulp of ln g are lost (precision-study
                                    demonstration; always runs on the thread sampler) */
 
+/* Where the warp sampler keeps a walker's screen and visit counts during a
+ * launch (rewl_config.table_mode); every choice gives the same trajectory. */
+#define REWL_TABLES_AUTO 0      /* staged when the window's bins fit in shared memory, else global */
+#define REWL_TABLES_GLOBAL 1    /* global memory (L1-cached) */
+#define REWL_TABLES_STAGED 2    /* all of the walker's bins in shared memory for the launch (REWL_E_CUDA
+                                   at launch when they do not fit) */
+
 /* Sampling kernels (same trajectory, different mapping onto the GPU). */
 #define REWL_SAMPLER_WARP 0     /* 8/16/32 lanes per walker, 3/4/5 trials resolved per step */
 #define REWL_SAMPLER_THREAD 1   /* one thread per walker, one trial per step */
@@ -106,6 +113,9 @@ typedef struct rewl_config {
     int32_t lanes_per_walker;   /* warp sampler: 8, 16 or 32 lanes per walker (0 = automatic) */
     uint64_t seed;              /* Philox key of every random draw */
     uint64_t drive_budget;      /* steps allowed to drive a walker into its window */
+    int32_t table_mode;         /* warp sampler: where a launch reads and writes S and H
+                                   (REWL_TABLES_*; the trajectory is the same in each) */
+    int32_t reserved;
 } rewl_config;
 
 /* Snapshot of a run. */

@@ -149,6 +149,7 @@ int check_config(const rewl_config *c, const char **why)
     if (c->sampler != REWL_SAMPLER_WARP && c->sampler != REWL_SAMPLER_THREAD) { *why = "unknown sampler"; return REWL_E_INVALID; }
     if (c->sampler == REWL_SAMPLER_WARP && c->walkers_per_block > 8) { *why = "warp sampler: walkers_per_block (warps per block) must be in [0, 8]"; return REWL_E_INVALID; }
     if (c->lanes_per_walker != 0 && c->lanes_per_walker != 8 && c->lanes_per_walker != 16 && c->lanes_per_walker != 32) { *why = "lanes_per_walker must be 0, 8, 16 or 32"; return REWL_E_INVALID; }
+    if (c->table_mode < REWL_TABLES_AUTO || c->table_mode > REWL_TABLES_STAGED) { *why = "unknown table_mode"; return REWL_E_INVALID; }
     return REWL_OK;
 }
 
@@ -441,8 +442,12 @@ int create_impl(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_
     // the walkers alone can fill the GPU
     if (cfg->lanes_per_walker) p.group = cfg->lanes_per_walker;
     else p.group = p.n_active_walkers <= 1216 ? 32 : (p.n_active_walkers <= 2432 ? 16 : 8);
-    p.smt = (p.sampler == REWL_SAMPLER_WARP &&
-             tree_smem_per_warp(p, true) * (size_t)(32 / p.group) <= 100 * 1024) ? 1 : 0;
+    // where the warp sampler keeps S and H during a launch: staged in shared
+    // memory when a warp's share stays small, else global memory
+    if (cfg->table_mode == REWL_TABLES_STAGED) p.smt = 1;
+    else if (cfg->table_mode == REWL_TABLES_GLOBAL) p.smt = 0;
+    else p.smt = tree_smem_per_warp(p, true) * (size_t)(32 / p.group) <= 100 * 1024 ? 1 : 0;
+    if (p.sampler != REWL_SAMPLER_WARP) p.smt = 0;
     h->first_active = -1;
     for (int win = 0; win < d.nwin && h->first_active < 0; ++win)
         if (active[win]) h->first_active = win * d.W;

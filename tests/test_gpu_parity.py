@@ -111,6 +111,29 @@ def test_sweep_bit_exact_single_window(P, L, sampler, lanes, prec):
         _compare(o, g)
 
 
+@pytest.mark.parametrize("L,nE,nM,W", [(24, 2, 2, 3), (48, 4, 2, 2), (64, 4, 2, 2), (8, 3, 3, 4)])
+@pytest.mark.parametrize("lanes", [32, 16, 8])
+def test_table_modes_bit_exact(P, L, nE, nM, W, lanes):
+    """Both places the warp sampler can keep S and H during a launch (global
+    memory; all of a walker's bins staged in shared memory, where they fit)
+    follow the oracle's chain, through exchanges and checks, in both exact
+    formats, for every group size."""
+    modes = [P.TABLES_GLOBAL] + ([P.TABLES_STAGED] if L <= 8 else [])
+    for prec in (0, 1):
+        kw = dict(L=L, n_win_E=nE, n_win_M=nM, walkers_per_window=W, exchange_interval=4000, seed=91 + L,
+                  drive_budget=10**8, lanes_per_walker=lanes, precision=prec)
+        o = OracleREWL(OracleConfig(**{k: v for k, v in kw.items() if k in OracleConfig.__dataclass_fields__}))
+        runs = [P.REWL(P.Config(table_mode=m, **kw)) for m in modes]
+        for chunk in (1, 6):
+            o.run_cycles(chunk)
+            for g in runs:
+                g.run_cycles(chunk)
+                _compare(o, g)
+        for g in runs:
+            g.close()
+        o.close()
+
+
 @pytest.mark.parametrize("sampler,prec", [(0, 0), (0, 1), (1, 0), (1, 1)])
 def test_cycles_bit_exact_L8_3x3(P, sampler, prec):
     """The 2D REWL workload at L = 8 (3 x 3 windows at 75% overlap, 4 walkers
