@@ -71,6 +71,12 @@ extern "C" {
 #define REWL_TABLES_STAGED 2    /* all of the walker's bins in shared memory for the launch (REWL_E_CUDA
                                    at launch when they do not fit) */
 
+/* How the warp sampler holds a walker's lattice during a launch
+ * (rewl_config.lattice_mode); every choice gives the same trajectory. */
+#define REWL_LATTICE_AUTO 0     /* a register when N <= 64, else shared memory */
+#define REWL_LATTICE_REGISTER 1 /* one 64-bit register per lane (N <= 64 only, else REWL_E_INVALID) */
+#define REWL_LATTICE_SHARED 2   /* one 32-bit word per row in shared memory (two for L > 32) */
+
 /* Sampling kernels (same trajectory, different mapping onto the GPU). */
 #define REWL_SAMPLER_WARP 0     /* 8/16/32 lanes per walker, 3/4/5 trials resolved per step */
 #define REWL_SAMPLER_THREAD 1   /* one thread per walker, one trial per step */
@@ -115,7 +121,8 @@ typedef struct rewl_config {
     uint64_t drive_budget;      /* steps allowed to drive a walker into its window */
     int32_t table_mode;         /* warp sampler: where a launch reads and writes S and H
                                    (REWL_TABLES_*; the trajectory is the same in each) */
-    int32_t reserved;
+    int32_t lattice_mode;       /* warp sampler: how a launch holds the lattice (REWL_LATTICE_*;
+                                   the trajectory is the same in each) */
 } rewl_config;
 
 /* Snapshot of a run. */

@@ -150,6 +150,8 @@ int check_config(const rewl_config *c, const char **why)
     if (c->sampler == REWL_SAMPLER_WARP && c->walkers_per_block > 8) { *why = "warp sampler: walkers_per_block (warps per block) must be in [0, 8]"; return REWL_E_INVALID; }
     if (c->lanes_per_walker != 0 && c->lanes_per_walker != 8 && c->lanes_per_walker != 16 && c->lanes_per_walker != 32) { *why = "lanes_per_walker must be 0, 8, 16 or 32"; return REWL_E_INVALID; }
     if (c->table_mode < REWL_TABLES_AUTO || c->table_mode > REWL_TABLES_STAGED) { *why = "unknown table_mode"; return REWL_E_INVALID; }
+    if (c->lattice_mode < REWL_LATTICE_AUTO || c->lattice_mode > REWL_LATTICE_SHARED) { *why = "unknown lattice_mode"; return REWL_E_INVALID; }
+    if (c->lattice_mode == REWL_LATTICE_REGISTER && c->L * c->L > 64) { *why = "a register lattice needs N <= 64"; return REWL_E_INVALID; }
     return REWL_OK;
 }
 
@@ -442,6 +444,7 @@ int create_impl(const rewl_config *cfg, const uint8_t *host_init_spins, void *d_
     // the walkers alone can fill the GPU
     if (cfg->lanes_per_walker) p.group = cfg->lanes_per_walker;
     else p.group = p.n_active_walkers <= 1216 ? 32 : (p.n_active_walkers <= 2432 ? 16 : 8);
+    p.lattice_reg = (cfg->lattice_mode == REWL_LATTICE_SHARED || d.N > 64 || d.wpr != 1) ? 0 : 1;
     // where the warp sampler keeps S and H during a launch: staged in shared
     // memory when a warp's share stays small, else global memory
     if (cfg->table_mode == REWL_TABLES_STAGED) p.smt = 1;

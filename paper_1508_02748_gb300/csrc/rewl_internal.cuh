@@ -73,6 +73,7 @@ struct Params {
     int sampler;      // REWL_SAMPLER_WARP or REWL_SAMPLER_THREAD
     int smt;          // warp sampler: tables staged in shared memory
     int group;        // warp sampler: lanes per walker
+    int lattice_reg;  // warp sampler: the lattice in a 64-bit register (N <= 64)
     uint32_t key0, key1;
     uint32_t divL;    // ceil(2^32 / L): site / L = umulhi(site, divL) for site < N
     double lnf_final, lnf_factor;

@@ -482,7 +482,7 @@ cudaError_t launch_sweep_tree(const Params &p, uint64_t ntrials, int group, int 
         return cudaGetLastError();
     };
 #define REWL_TREE_G(W_, S_, P_)                                            \
-    if (p.N <= 64 && W_ == 1) {                                            \
+    if (p.lattice_reg && W_ == 1) {                                        \
         if (group == 32) return go(k_sweep_tree<1, S_, 32, P_, true>);     \
         if (group == 16) return go(k_sweep_tree<1, S_, 16, P_, true>);     \
         return go(k_sweep_tree<1, S_, 8, P_, true>);                       \

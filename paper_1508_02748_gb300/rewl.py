@@ -25,6 +25,7 @@ PART_SAMPLE, PART_REST, PART_SAMPLE_PLAIN = 1, 2, 4
 SAMPLER_WARP, SAMPLER_THREAD = 0, 1
 LNG_JOINED, LNG_MARGINAL_E = 0, 1
 TABLES_AUTO, TABLES_GLOBAL, TABLES_STAGED = 0, 1, 2
+LATTICE_AUTO, LATTICE_REGISTER, LATTICE_SHARED = 0, 1, 2
 JOIN_MARGINAL, JOIN_PER_SLICE = 0, 0x100   # rescaling rule of a join step, OR-ed into `what`
 
 
@@ -44,7 +45,7 @@ class rewl_config(ctypes.Structure):
                 ("exchange_interval", ctypes.c_uint64), ("check_every", ctypes.c_int32),
                 ("walkers_per_block", ctypes.c_int32), ("sampler", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32),
                 ("seed", ctypes.c_uint64),
-                ("drive_budget", ctypes.c_uint64), ("table_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("drive_budget", ctypes.c_uint64), ("table_mode", ctypes.c_int32), ("lattice_mode", ctypes.c_int32)]
 
 
 class rewl_status(ctypes.Structure):
@@ -149,13 +150,13 @@ class Config:
     seed: int = 1
     drive_budget: int = 10_000_000
     table_mode: int = 0
+    lattice_mode: int = 0
 
     def to_c(self) -> rewl_config:
         c = rewl_config()
         c.struct_size = ctypes.sizeof(rewl_config)
         for name, _ in rewl_config._fields_[1:]:
-            if name != "reserved":
-                setattr(c, name, getattr(self, name))
+            setattr(c, name, getattr(self, name))
         return c
 
     @classmethod
@@ -322,7 +323,7 @@ class REWL:
         lib = load_library()
         c = rewl_config()
         _check(lib.rewl_checkpoint_config(os.fsencode(path), ctypes.byref(c)))
-        kw = {name: getattr(c, name) for name, _ in rewl_config._fields_[1:] if name != "reserved"}
+        kw = {name: getattr(c, name) for name, _ in rewl_config._fields_[1:]}
         self = cls.__new__(cls)
         self.cfg = Config(**kw)
         self._c = c

@@ -56,6 +56,14 @@ def test_workspace_size_and_validation_without_gpu():
     for kw in (dict(lnf_init=4.0), dict(lnf_factor=0.25), dict(lnf_init=2.0 ** -27)):
         ok = P.Config(L=8, **kw).to_c()
         assert lib.rewl_workspace_size(ctypes.byref(ok), ctypes.byref(n)) == 0
+    # placement knobs: unknown values are refused; a register lattice needs N <= 64
+    for kw in (dict(table_mode=3), dict(lattice_mode=-1), dict(L=12, lattice_mode=P.LATTICE_REGISTER)):
+        bad = P.Config(**{"L": 8, **kw}).to_c()
+        assert lib.rewl_workspace_size(ctypes.byref(bad), ctypes.byref(n)) == -1
+    for kw in (dict(lattice_mode=P.LATTICE_REGISTER), dict(L=12, lattice_mode=P.LATTICE_SHARED),
+               dict(table_mode=P.TABLES_STAGED), dict(table_mode=P.TABLES_GLOBAL)):
+        ok = P.Config(**{"L": 8, **kw}).to_c()
+        assert lib.rewl_workspace_size(ctypes.byref(ok), ctypes.byref(n)) == 0
 
 
 def test_product_path_has_no_cpu_fallback():

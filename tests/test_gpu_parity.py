@@ -116,14 +116,18 @@ def test_sweep_bit_exact_single_window(P, L, sampler, lanes, prec):
 def test_table_modes_bit_exact(P, L, nE, nM, W, lanes):
     """Both places the warp sampler can keep S and H during a launch (global
     memory; all of a walker's bins staged in shared memory, where they fit)
-    follow the oracle's chain, through exchanges and checks, in both exact
-    formats, for every group size."""
-    modes = [P.TABLES_GLOBAL] + ([P.TABLES_STAGED] if L <= 8 else [])
+    and both places it can keep a small lattice (N <= 64: one register, or
+    shared memory like a larger one) follow the oracle's chain, through
+    exchanges and checks, in both exact formats, for every group size."""
+    modes = [(P.TABLES_GLOBAL, P.LATTICE_AUTO)] + ([(P.TABLES_STAGED, P.LATTICE_AUTO)] if L <= 8 else [])
+    if L <= 8:
+        modes += [(P.TABLES_GLOBAL, P.LATTICE_SHARED), (P.TABLES_STAGED, P.LATTICE_SHARED),
+                  (P.TABLES_AUTO, P.LATTICE_REGISTER)]
     for prec in (0, 1):
         kw = dict(L=L, n_win_E=nE, n_win_M=nM, walkers_per_window=W, exchange_interval=4000, seed=91 + L,
                   drive_budget=10**8, lanes_per_walker=lanes, precision=prec)
         o = OracleREWL(OracleConfig(**{k: v for k, v in kw.items() if k in OracleConfig.__dataclass_fields__}))
-        runs = [P.REWL(P.Config(table_mode=m, **kw)) for m in modes]
+        runs = [P.REWL(P.Config(table_mode=t, lattice_mode=m, **kw)) for t, m in modes]
         for chunk in (1, 6):
             o.run_cycles(chunk)
             for g in runs:
