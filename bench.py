@@ -68,8 +68,9 @@ BYTES_PER_TRIAL = 40
 
 # Counters of the sampling kernel from ncu captures (their summaries are in
 # the profiles directory), per launch in the benchmark's launch
-# configuration, keyed by workload, kernel, table format, lanes per walker
-# and the hash of the kernel sources (any other case reports null):
+# configuration, keyed by workload, kernel, table format, lanes per walker,
+# table and lattice placement (as configured; 0 = automatic) and the hash of
+# the kernel sources (any other case reports null):
 # dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum of one launch;
 # warp_inst_per_trial = smsp__inst_executed.sum / trials of one launch.
 TRAFFIC_SOURCES = ("paper_1508_02748_gb300/csrc/rewl_sweep_tree.cu", "paper_1508_02748_gb300/csrc/rewl_tab.cuh",
@@ -78,10 +79,10 @@ PROFILE = {
     # L = 32, 16 x 4 windows, 32 walkers each, 32 lanes per walker: DRAM bytes from a one-pass capture
     # of the full workload after 512 warm-up cycles; instructions per trial from the full capture of
     # the same kernel at 16 walkers per window
-    ("rewl_L32_16x4_w32", "k_sweep_tree", "fp64", 32, "a08a3138e84675cd"): {"dram_bytes": 142_710_000,
+    ("rewl_L32_16x4_w32", "k_sweep_tree", "fp64", 32, 0, 0, "a08a3138e84675cd"): {"dram_bytes": 142_710_000,
                                                                "warp_inst_per_trial": 53.22},
     # L = 8, 3 x 3 windows, 4 walkers each, 32 lanes per walker (tables staged in shared memory)
-    ("rewl_L8_3x3_w4", "k_sweep_tree", "fp64", 32, "a08a3138e84675cd"): {"dram_bytes": 607_488,
+    ("rewl_L8_3x3_w4", "k_sweep_tree", "fp64", 32, 0, 0, "a08a3138e84675cd"): {"dram_bytes": 607_488,
                                                             "warp_inst_per_trial": 61.30},
 }
 
@@ -126,6 +127,10 @@ def parse():
                     help="warp sampler: lanes per walker (fixes the tiling, no autotuning)")
     ap.add_argument("--wpb", type=int, default=None,
                     help="warps (warp sampler) or threads (thread sampler) per block (fixes the tiling)")
+    ap.add_argument("--tables", choices=["auto", "global", "staged"], default="auto",
+                    help="with --lanes/--wpb: where the warp sampler keeps S and H")
+    ap.add_argument("--lattice", choices=["auto", "register", "shared"], default="auto",
+                    help="with --lanes/--wpb: where the warp sampler keeps a lattice of N <= 64 sites")
     ap.add_argument("--lnf-final", type=float, default=None, help="override the workload's final ln f")
     ap.add_argument("--walkers-per-window", type=int, default=None,
                     help="override the workload's walkers per window (small cases for profiler captures)")
@@ -137,6 +142,8 @@ def parse():
                     help="auto: the autotuner picks the sampler too (with --no-autotune: warp)")
     ap.add_argument("--replicate", type=int, default=0,
                     help="seed replicate of the run (seed 20150811 + 1000 workload id + replicate + rank)")
+    ap.add_argument("--replicates", type=int, default=1,
+                    help="--impl reference --time-to: seeds run at once, one process each")
     ap.add_argument("--form", default="batched", choices=["batched", "plain"],
                     help="plain: each walker's trials as a launch of their own (one thread, 4 streams), "
                          "exchange and check launched from the host, no graph; same trajectory")
@@ -351,6 +358,60 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_time_to_worker(task):
+    """One host process: the oracle run of workload `w` with seed `seed` from
+    creation to its final ln f (or `seconds` of wall time), polled every 64
+    checks like the GPU run; returns its time, cycles and E-marginal error."""
+    w, seed, seconds = task
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    r = oracle.OracleREWL(_oracle_cfg(w, w.walkers_per_window, seed))
+    t0 = time.perf_counter()
+    capped = False
+    while not r.info()["done"]:
+        r.run_cycles(64 * w.check_every)
+        if time.perf_counter() - t0 > seconds:
+            capped = True
+            break
+    dt = time.perf_counter() - t0
+    inf = r.info()
+    eps = None
+    ex = exact_lngE(w.L)
+    if ex is None and w.L <= 6:                # small lattices: g(E) by enumeration
+        g = oracle.enumerate_gEM(w.L).sum(axis=1)
+        with np.errstate(divide="ignore"):
+            ex = np.where(g > 0, np.log(np.where(g > 0, g, 1)), -np.inf)
+    if ex is not None and not capped:
+        J, _, _ = r.join()
+        mE = oracle.marginal_e(J)
+        ok = np.isfinite(ex) & (ex > 0) & np.isfinite(mE)
+        eps = float(np.mean(np.abs(mE[ok] - ex[ok]) / ex[ok]))
+    r.close()
+    return {"seed": seed, "seconds": dt, "capped": capped, "cycles": inf["cycle"], "iterations": inf["iter"],
+            "mean_eps_E_marginal_vs_exact": eps}
+
+
+def run_reference_time_to(args, w):
+    """The CPU oracle's time to the workload's final ln f: `--replicates` seeds
+    (replicate, replicate + 1, ...), each run to done on one core in its own
+    spawned process, all at once."""
+    import multiprocessing as mp
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return
+    n = max(1, args.replicates)
+    tasks = [(w, w.seed(args.replicate + k), args.max_seconds) for k in range(n)]
+    with mp.get_context("spawn").Pool(min(n, host_cores())) as pool:
+        runs = pool.map(_oracle_time_to_worker, tasks)
+    secs = [r["seconds"] for r in runs]
+    line = {"metric": "time-to-ln f<=%g" % w.lnf_final, "value": sum(secs) / len(secs), "unit": "s",
+            "higher_is_better": False, "impl": "reference", "dtype": "f64", "data": "synthetic",
+            "config": _config_dict(w, "none (CPU)"), "cpu_model": cpu_model(),
+            "cores_per_run": 1, "runs": runs}
+    print(json.dumps(line), flush=True)
+
+
 def _sampler_name(code: int) -> str:
     return "warp" if code == 0 else "thread"
 
@@ -502,7 +563,11 @@ def run_gpu(args, w):
     plain = args.form == "plain"
     if args.lanes is not None or args.wpb is not None:
         import dataclasses
-        cfg = dataclasses.replace(cfg, lanes_per_walker=args.lanes or 0, walkers_per_block=args.wpb or 0)
+        cfg = dataclasses.replace(cfg, lanes_per_walker=args.lanes or 0, walkers_per_block=args.wpb or 0,
+                                  table_mode={"auto": P.TABLES_AUTO, "global": P.TABLES_GLOBAL,
+                                              "staged": P.TABLES_STAGED}[args.tables],
+                                  lattice_mode={"auto": P.LATTICE_AUTO, "register": P.LATTICE_REGISTER,
+                                                "shared": P.LATTICE_SHARED}[args.lattice])
     elif not args.no_autotune and not plain:
         from paper_1508_02748_gb300.autotune import autotune
         allowed = (P.SAMPLER_WARP, P.SAMPLER_THREAD) if args.sampler == "auto" else (smp,)
@@ -584,7 +649,8 @@ def run_gpu(args, w):
     sweep_s = statistics.mean(sweep_ms) / 1e3
     achieved = OPS_PER_TRIAL * trials_per_step / sweep_s
     kname = "k_sweep_tree" if cfg.sampler == P.SAMPLER_WARP and not plain and prec != P.F32 else "k_sweep_thread"
-    prof = PROFILE.get((w.name, kname, args.precision, cfg.lanes_per_walker, sources_hash())) if not plain else None
+    prof = PROFILE.get((w.name, kname, args.precision, cfg.lanes_per_walker, cfg.table_mode, cfg.lattice_mode,
+                        sources_hash())) if not plain else None
     traffic = prof["dram_bytes"] if prof else None
     if peaks:
         peak_ops = peaks["lop3_ops_per_s"]
@@ -663,7 +729,9 @@ def run_gpu(args, w):
                                             args.precision, "thread" if plain else _sampler_name(cfg.sampler)),
                                form=args.form, state=state,
                                tiling={"sampler": cfg.sampler, "lanes_per_walker": cfg.lanes_per_walker,
-                                       "walkers_per_block": cfg.walkers_per_block}),
+                                       "walkers_per_block": cfg.walkers_per_block,
+                                       "tables": ["auto", "global", "staged"][cfg.table_mode],
+                                       "lattice": ["auto", "register", "shared"][cfg.lattice_mode]}),
                 "roofline": roof, "plain": plain_line, "time_to": tt, "others": others, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * world, "clocks": clk, "peaks": peaks,
                 "run": {"iteration": st["iteration"], "lnf": st["lnf"], "exch_accepts": st["exch_accepts"],
@@ -1070,7 +1138,10 @@ def main():
         run_gpu_batch(args)
         return
     if args.impl == "reference":
-        run_reference(args, w)
+        if args.time_to:
+            run_reference_time_to(args, w)
+        else:
+            run_reference(args, w)
     else:
         run_gpu(args, w)
 

@@ -1,7 +1,7 @@
 """bench.py's reference arm (the CPU oracle on every host core) on CPU: one
 JSON line with the keys the benchmark contract names, on the same metric,
-unit and workload as the GPU arm, and a refusal to run the batch workload's
-~35 GB of tables."""
+unit and workload as the GPU arm, a refusal to run the batch workload's
+~35 GB of tables, and the oracle's time to the final ln f."""
 import json
 import os
 import subprocess
@@ -50,3 +50,18 @@ def test_reference_arm_warmup_floor():
 def test_reference_arm_refuses_batch():
     d = _run("--impl", "reference", "--workload", "batch_24_mixed_L16_24_32_48", "--steps", "1")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_reference_time_to_serial_L4():
+    """The oracle run to its final ln f, seed by seed: the serial L = 4 walker
+    (one window, one walker) meets the enumerated g(E) to a few percent, and a
+    seed gives the same run twice."""
+    d = _run("--impl", "reference", "--time-to", "--workload", "serial_wl_L4", "--replicates", "2")
+    assert d["impl"] == "reference" and d["unit"] == "s" and d["higher_is_better"] is False
+    assert [r["seed"] for r in d["runs"]] == [20151811, 20151812]
+    for r in d["runs"]:
+        assert not r["capped"] and r["iterations"] == 21
+        assert 0 < r["mean_eps_E_marginal_vs_exact"] < 0.026
+    again = _run("--impl", "reference", "--time-to", "--workload", "serial_wl_L4", "--replicate", "1")
+    assert again["runs"][0]["cycles"] == d["runs"][1]["cycles"]
+    assert again["runs"][0]["mean_eps_E_marginal_vs_exact"] == d["runs"][1]["mean_eps_E_marginal_vs_exact"]
