@@ -86,7 +86,9 @@ struct RingEntry {
     float lnu;     // ln u in float
 };
 
-// Per-walker exchange area of one step (shared memory).
+// Per-walker exchange area of one step (shared memory, 16-byte aligned: it
+// follows the ring).  The leaf's four words are written and read as one
+// 16-byte vector.
 struct Mailbox {
     int fsite[8];                  // register lattice: bit index flipped by trial t+k, 64 if none
     int leafC;                     // position e << 16 | m after the last trial
@@ -94,6 +96,8 @@ struct Mailbox {
     int leafq;                     // its H as read this step (>= 0)
     float leafs;                   // its screen value
 };
+static_assert(offsetof(Mailbox, leafC) % 16 == 0 && (RING * sizeof(RingEntry)) % 16 == 0,
+              "the leaf's post must be 16-byte aligned");
 
 // Eq. 1 decided from the exact values (near-ties of the float screen only);
 // kept out of line so none of it runs in the common case.  ccnt and ncnt
@@ -340,8 +344,12 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         // ---- 3. decision of the own trial (Eq. 1); off-path lanes may hold
         // positions outside the window, so their reads are clamped
         const unsigned cu = min((unsigned)cidx, Tm1), nu = min((unsigned)nidx, Tm1);
-        const float cs_m = S[cu], ns_m = S[nu];
-        const int hc = max(Hh[cu], 0), hn = max(Hh[nu], 0);
+        // a lane whose bin is the walker's committed bin takes S and H from
+        // registers (base32, lq); with the tables in global memory it also
+        // skips their load (in shared memory the predicate costs more than the load)
+        const bool c0p = !SMT && Pc == P0, n0p = !SMT && Pn == P0;
+        const float cs_m = c0p ? 0.f : S[cu], ns_m = n0p ? 0.f : S[nu];
+        const int hc = c0p ? 0 : max(Hh[cu], 0), hn = n0p ? 0 : max(Hh[nu], 0);
         int vcur = 0, vnew = 0;
         #pragma unroll
         for (int k = 0; k < DEPTH; ++k) {
@@ -374,12 +382,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         const unsigned aidx = acc ? nu : cu;
         if (onp) {
             if (REG) box->fsite[dl] = acc ? (int)(me.a & 63u) : 64;
-            if (dl == D) {
-                box->leafC = after;
-                box->leafcC = cupto;
-                box->leafq = aq;
-                box->leafs = acc ? ns : cs;
-            }
+            if (dl == D)      // one 16-byte store: position, visits, H, screen
+                *reinterpret_cast<int4 *>(&box->leafC) = make_int4(after, cupto, aq, __float_as_int(acc ? ns : cs));
             err |= val < 0;
         }
         // H of the bins visited in this step, in path order: the pending count of
@@ -394,7 +398,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
             if (onp && dl == k) Hh[aidx] = val;
         }
         __syncwarp(gmask);
-        const int C = box->leafC, cC = box->leafcC;
+        const int4 lb = *reinterpret_cast<const int4 *>(&box->leafC);   // the leaf's post
+        const int C = lb.x, cC = lb.y;
         if (REG) {
             #pragma unroll
             for (int k = 0; k <= DEPTH; ++k) {
@@ -410,8 +415,8 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         // the group adopts the state after the last trial
         {
             const bool same = C == P0;
-            const int nlq = (same ? lq : box->leafq) + cC;
-            const float ns32 = box->leafs;
+            const int nlq = (same ? lq : lb.z) + cC;
+            const float ns32 = __int_as_float(lb.w);
             hq = same ? hq + cC : cC;
             lq = nlq;
             err |= nlq < 0;
