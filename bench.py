@@ -79,10 +79,10 @@ PROFILE = {
     # L = 32, 16 x 4 windows, 32 walkers each, 32 lanes per walker: DRAM bytes from a one-pass capture
     # of the full workload after 512 warm-up cycles; instructions per trial from the full capture of
     # the same kernel at 16 walkers per window
-    ("rewl_L32_16x4_w32", "k_sweep_tree", "fp64", 32, 0, 0, "b681e2f1638020f3"): {"dram_bytes": 143_030_016,
+    ("rewl_L32_16x4_w32", "k_sweep_tree", "fp64", 32, 0, 0, "3eb3a9b855675b6e"): {"dram_bytes": 143_505_408,
                                                                "warp_inst_per_trial": 53.22},
     # L = 8, 3 x 3 windows, 4 walkers each, 32 lanes per walker (tables staged in shared memory)
-    ("rewl_L8_3x3_w4", "k_sweep_tree", "fp64", 32, 0, 0, "b681e2f1638020f3"): {"dram_bytes": 608_000,
+    ("rewl_L8_3x3_w4", "k_sweep_tree", "fp64", 32, 0, 0, "3eb3a9b855675b6e"): {"dram_bytes": 608_256,
                                                             "warp_inst_per_trial": 60.50},
 }
 

@@ -362,7 +362,10 @@ __global__ void __launch_bounds__(256) k_sweep_tree(Params p, unsigned ntrials, 
         const float c32 = __fmaf_rn(__int2float_rn(ccnt), lnf32, cs);
         const float n32 = __fmaf_rn(__int2float_rn(ncnt), lnf32, ns);
         const float d32 = __fsub_rn(c32, n32);
-        const float M = __fmaf_rn(fabsf(c32) + fabsf(n32) + fabsf(cs) + fabsf(ns) + fabsf(me.lnu), 0x1p-20f, 0x1p-20f);
+        // the terms known before c and n are summed first (shorter chain; the
+        // margin's factor-two slack over the error bound covers either order)
+        const float M = __fmaf_rn((fabsf(c32) + fabsf(n32)) + (fabsf(cs) + fabsf(ns) + fabsf(me.lnu)), 0x1p-20f,
+                                  0x1p-20f);
         int acc = (me.lnu < d32 - M) ? 1 : 0;
         if (live && !acc && !(me.lnu > d32 + M))
             acc = exact_accept<TB>(g_base, cu, ccnt, nu, ncnt, lnf, me.xu, me.lnu);
