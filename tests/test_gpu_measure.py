@@ -58,3 +58,24 @@ def test_table_digest_follows_the_tables(P):
     assert a.digest() != d0                         # one ln g value moved by 2^-20
     a.set_tables(la, Ha)
     assert a.digest() == d0
+
+
+def test_autotuned_tiling_keeps_the_trajectory(P):
+    """The autotuner times every tiling and placement on the actual
+    configuration; whichever it returns runs the same chain as the default
+    tiling (same table digest and walker states after whole cycles)."""
+    from paper_1508_02748_gb300.autotune import autotune
+    cfg = P.Config(L=8, n_win_E=2, n_win_M=2, walkers_per_window=3, exchange_interval=2000, seed=20152901)
+    tuned = autotune(cfg, cache_path=None, cycles=2)
+    assert tuned.sampler in (P.SAMPLER_WARP, P.SAMPLER_THREAD)
+    assert tuned.table_mode in (P.TABLES_AUTO, P.TABLES_GLOBAL)
+    assert tuned.lattice_mode in (P.LATTICE_AUTO, P.LATTICE_SHARED)
+    a, b = P.REWL(cfg), P.REWL(tuned)
+    a.run_cycles(40)
+    b.run_cycles(40)
+    assert a.digest() == b.digest()
+    sa, pa = a.walkers()
+    sb, pb = b.walkers()
+    assert np.array_equal(sa, sb) and np.array_equal(pa, pb)
+    a.close()
+    b.close()
